@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark of the ternary free-energy LB time step (arXiv:1511.02155) on GB300.
+
+A "step" is one full time step of the method over the whole lattice (moments,
+derivatives, chemical potentials, pressure-tensor equilibria, BGK collision,
+streaming, FP64 mass totals).  Metric: million lattice-node updates per second
+(MLUPS) and the step kernel's fraction of the measured HBM roofline.
+
+Default workload: D3Q19 256^3 periodic ternary spinodal decomposition (FP32),
+populations 3.8 GB per copy (larger than L2, so every step streams from HBM).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload spinodal256|lens512|probe8192] [--precision fp32|fp64|fp16|bf16]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on
+its own GPU (weak scaling, no collective in the data path); timing takes the
+maximum over ranks and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1511_02155_gb300 import workloads as W  # noqa: E402
+
+METRIC = "MLUPS and % HBM roofline per ternary step (FP32 vs FP16-store) at fixed error"
+STORE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def workload(name: str):
+    if name == "spinodal256":
+        return W.spinodal_3d(256, seed=3), "D3Q19 256^3 periodic ternary spinodal decomposition"
+    if name == "lens512":
+        return W.lens_512x256(), "D2Q9 512x256 periodic liquid lens, radius 60 (L2-resident)"
+    if name == "probe8192":
+        return W.probe_2d(8192), "D2Q9 8192^2 periodic ternary spinodal mixture"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_from_profiles(kernel_tag: str, source_digest: str):
+    """DRAM bytes per launch from a committed ncu summary, or None if the summary
+    is missing or was taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel_tag)
+    if not e or e.get("source_sha256") != source_digest:
+        return None
+    return float(e["dram_bytes_per_launch"])
+
+
+def kernel_source_digest():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1511_02155_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cuh", ".cu", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows
+                                    if r[3].replace(".", "").isdigit()), default=None)}
+
+
+def cpu_baseline(cfg_name: str, cfg: dict, budget_s: float = 12.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    the same recipe on a smaller lattice, OpenMP over all host cores."""
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+    Q = cfg["Q"]
+    if Q == 19:
+        n = 48
+        C = W.spinodal((n, n, n), seed=3)
+        shape = (n, n, n)
+        sample = f"D3Q19 {n}^3 sub-lattice of the same spinodal recipe"
+    else:
+        ny, nx = (128, 256) if cfg_name == "lens512" else (256, 256)
+        if cfg_name == "lens512":
+            C = W.lens(nx, ny, 30.0, 1.0, 0.0, 64.0, (128.0, 64.0))
+        else:
+            C = W.spinodal((ny, nx), seed=5)
+        shape = (nx, ny, 1)
+        sample = f"D2Q9 {nx}x{ny} sub-lattice of the same recipe"
+    p = oracle.make_params(Q, *shape, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"], cfg["M_psi"])
+    f, g, k = oracle.init_equilibrium(p, *W.to_aux(*C))
+    N = int(np.prod(shape))
+    t0 = time.perf_counter()
+    oracle.step(p, f, g, k, 1)
+    one = time.perf_counter() - t0
+    nsteps = max(1, int(budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.step(p, f, g, k, nsteps)
+    dt = time.perf_counter() - t0
+    return {"value": round(N * nsteps / dt / 1e6, 4), "unit": "MLUPS",
+            "cores": int(os.environ.get("OMP_NUM_THREADS", cores)), "kind": "oracle",
+            "sample": f"{sample}, {nsteps} steps ({dt:.1f} s, FP64)"}
+
+
+def run_reference(args, cfg_name, cfg, label):
+    """Reference arm: the FP64 CPU oracle on a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    import oracle
+    Q = cfg["Q"]
+    if Q == 19:
+        n = 32
+        C = W.spinodal((n, n, n), seed=3)
+        shape = (n, n, n)
+        sample = f"D3Q19 {n}^3 sub-lattice per step"
+    else:
+        C = W.spinodal((128, 128), seed=5) if cfg_name != "lens512" else W.lens(256, 128, 30.0, 1.0, 0.0, 64.0, (128.0, 64.0))
+        shape = (C[0].shape[1], C[0].shape[0], 1)
+        sample = f"D2Q9 {shape[0]}x{shape[1]} sub-lattice per step"
+    p = oracle.make_params(Q, *shape, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"], cfg["M_psi"])
+    f, g, k = oracle.init_equilibrium(p, *W.to_aux(*C))
+    N = int(np.prod(shape))
+    oracle.step(p, f, g, k, args.warmup)
+    t0 = time.perf_counter()
+    oracle.step(p, f, g, k, args.steps)
+    dt = time.perf_counter() - t0
+    v = N * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": round(v, 4), "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": label, "sample": sample, "lattice_nodes": N},
+            "cpu_baseline": {"value": round(v, 4), "unit": "MLUPS",
+                             "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="spinodal256", choices=["spinodal256", "lens512", "probe8192"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "split"])
+    ap.add_argument("--tile", default="0,0")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    cfg, label = workload(args.workload)
+
+    if args.impl == "reference":
+        run_reference(args, args.workload, cfg, label)
+        return
+
+    import torch
+    import paper_1511_02155_gb300 as tl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+
+    Q = cfg["Q"]
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    N = nx * ny * nz
+    if world > 1 and rank > 0 and cfg.get("C") is not None and Q == 19:
+        cfg["C"] = W.spinodal((nz, ny, nx), seed=3 + rank)  # an independent replica per rank
+    rho, phi, psi = W.to_aux(*cfg["C"])
+    cfg["C"] = None
+    eng = tl.TernaryLB(Q, nx, ny, nz, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"],
+                       cfg["M_psi"], cfg["h"], None, args.precision)
+    if args.kernel != "auto":
+        eng.set_kernel(args.kernel)
+    tv, tc = (int(v) for v in args.tile.split(","))
+    eng.set_tile(tv, tc)
+    eng.init_fields(rho, phi, psi)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    eng.step(args.warmup)
+    barrier()
+
+    # timed region: K steps, inputs (3.8 GB populations) far larger than L2
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        eng.step(args.steps)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    m_after = eng.step_mass()  # raises on a non-finite total
+    value = world * N * args.steps / (ms / 1e3) / 1e6
+
+    # main-kernel duration, CUDA events on the engine's stream around each launch
+    eng.set_timing(True)
+    eng.step(min(args.steps, 50))
+    kms, ksteps = eng.kernel_time()
+    eng.set_timing(False)
+    kernel_ms = kms / max(ksteps, 1)
+    s = STORE_BYTES[args.precision]
+    alg_bytes = 2 * 3 * Q * s * N  # every population read once and written once
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    kind = eng.kernel
+    tag = f"{kind}:{args.workload}:{args.precision}"
+    traffic = traffic_from_profiles(tag, kernel_source_digest())
+
+    # end to end through the public API with host buffers: upload the fields from
+    # pinned memory, K steps, download C_1..3 and the mass totals
+    pin = [torch.from_numpy(np.ascontiguousarray(a.reshape(-1))).pin_memory() for a in (rho, phi, psi)]
+    outs = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(3)]
+    barrier()
+    t0 = time.perf_counter()
+    eng.init_from_host_ptrs(*(t.data_ptr() for t in pin))
+    eng.step(args.steps)
+    eng.fields_into(*(t.data_ptr() for t in outs))
+    _ = eng.mass()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": round(world * N * args.steps / e2e_s / 1e6, 2), "unit": "MLUPS",
+           "h2d_bytes_per_step": round(3 * 8 * N / args.steps, 1),
+           "d2h_bytes_per_step": round((3 * 8 * N + 24) / args.steps, 1),
+           "job": f"upload rho/phi/psi (fp64, pinned) + equilibrium init, {args.steps} steps, "
+                  "download C1..C3 (fp64) + mass totals"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-store/f32",
+                                           "bf16": "bf16-store/f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": label, "nodes_per_gpu": N, "lattice": f"D{3 if Q == 19 else 2}Q{Q}",
+                       "precision": args.precision, "kernel": kind,
+                       "l2": "populations exceed L2 (no flush needed)" if alg_bytes / 2 > 129e6
+                       else "L2-resident lattice", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                         "kernel_ms": round(kernel_ms, 4),
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "bytes_per_node": 2 * 3 * Q * s},
+            "e2e": e2e,
+            "gpu_launches": args.steps * eng.launches_per_step,
+            "clocks": clocks,
+            "mass_totals": [float(v) for v in m_after],
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload, cfg)
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

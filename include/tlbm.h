@@ -1,0 +1,213 @@
+/*
+ * tlbm.h -- C ABI of a single-GPU (sm_103a) engine for the ternary free-energy
+ * lattice Boltzmann method of Semprebon, Krueger and Kusumaatmaja,
+ * "Ternary free energy lattice Boltzmann model with tunable surface tensions and
+ * contact angles" (arXiv:1511.02155).
+ *
+ * One time step (tlbm_step) is the LBM section of the paper, in order:
+ *   moments rho = sum f, rho v = sum f e, phi = sum g, psi = sum k  (Eq. lbconstraint)
+ *   concentrations C1 = (rho+phi-psi)/2, C2 = (rho-phi-psi)/2, C3 = psi
+ *                                                  (Sec. Auxiliary variables)
+ *   wetting ghost values on solid nodes that impose the wall-normal gradients of
+ *   rho, phi, psi set by h_1..3                    (Sec. Auxiliary variables)
+ *   isotropic gradients and Laplacians; chemical potentials mu_rho, mu_phi, mu_psi
+ *   and bulk pressure p_b                          (Sec. Equations of Motion)
+ *   pressure-tensor equilibria f_eq, g_eq, k_eq    (Eq. eqdistfbinary)
+ *   BGK collision                                  (Eq. latboltCollision)
+ *   streaming with halfway bounce-back at solids   (Eq. latboltPropagation)
+ *   FP64 totals of rho, phi, psi over fluid nodes  (mass constraints closing the
+ *                                                   LBM section)
+ *
+ * Conventions
+ *   Lattice: D2Q9 (nz must be 1) or D3Q19.  Velocity order
+ *     D2Q9 : 0; (1,0) (-1,0) (0,1) (0,-1); (1,1) (-1,-1) (-1,1) (1,-1)
+ *     D3Q19: 0; +-x +-y +-z; (1,1,0) (1,-1,0) (-1,1,0) (-1,-1,0);
+ *            (0,1,1) (0,1,-1) (0,-1,1) (0,-1,-1); (1,0,1) (1,0,-1) (-1,0,1) (-1,0,-1)
+ *     (the D3Q19 order is the one the paper's weight table implies).
+ *   Node index: x + nx*(y + ny*z), x fastest.  All directions are periodic;
+ *   walls are made of solid nodes.
+ *   Populations exchanged with the host (tlbm_get_populations /
+ *   tlbm_set_populations) are conventional post-streaming values f_i(r, t) as
+ *   doubles, laid out [set f,g,k][i][node].  Solid nodes carry zeros.
+ *   Relaxation times: tau_rho = tau_f; tau_phi = 1/2 + M_phi/Gamma_phi and
+ *   tau_psi = 1/2 + M_psi/Gamma_psi (Eqs. Mobility1, Mobility2) with
+ *   Gamma_phi = Gamma_psi = 1 unless tlbm_set_gamma changes them.
+ *
+ * Ownership: the engine allocates and owns all device memory (cudaMalloc) of a
+ *   handle; every host pointer argument is read or written during the call only
+ *   and stays owned by the caller.
+ * Streams: all device work of a handle is queued on the CUDA stream given at
+ *   creation (NULL = the legacy default stream).  tlbm_step returns without
+ *   waiting; calls that return host data synchronise that stream.
+ * Errors: every call returns a tlbm_status; tlbm_last_error() gives a message.
+ *   Nothing throws across the ABI and no kernel traps.
+ * Threads: a handle must not be used from two host threads at once.
+ */
+#ifndef TLBM_H
+#define TLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tlbm tlbm; /* opaque handle */
+
+typedef enum {
+    TLBM_OK = 0,
+    TLBM_ERR_ARG = 1,         /* NULL handle/pointer, bad size, bad enum */
+    TLBM_ERR_PARAM = 2,       /* tau <= 1/2, kappa <= 0, |4 h/(alpha kappa)| >= 1, alpha <= 0 */
+    TLBM_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    TLBM_ERR_OOM = 4,         /* device allocation failed */
+    TLBM_ERR_NONFINITE = 5,   /* a mass total became NaN or Inf */
+    TLBM_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+    TLBM_ERR_UNSUPPORTED = 7  /* combination not built (e.g. kernel kind for this lattice) */
+} tlbm_status;
+
+typedef enum { TLBM_D2Q9 = 9, TLBM_D3Q19 = 19 } tlbm_lattice;
+
+/* Storage / arithmetic of the populations.
+ *   TLBM_FP64        : stored and computed in double.
+ *   TLBM_FP32        : stored and computed in float.
+ *   TLBM_FP16_OFFSET : stored in IEEE half as offsets from the rest state (f_i - w_i,
+ *                      g_i and k_i as is), computed in float.
+ *   TLBM_BF16_OFFSET : as above with bfloat16 storage. */
+typedef enum { TLBM_FP64 = 0, TLBM_FP32 = 1, TLBM_FP16_OFFSET = 2, TLBM_BF16_OFFSET = 3 } tlbm_precision;
+
+/* Which step implementation runs.
+ *   TLBM_KERNEL_FUSED: one kernel per step that marches through the lattice,
+ *                      recomputing halo moments on chip (no moment arrays).
+ *   TLBM_KERNEL_SPLIT: three kernels per step (moments to a device array,
+ *                      wetting ghosts, collide+stream).
+ *   TLBM_KERNEL_AUTO : FUSED where built, else SPLIT. */
+typedef enum { TLBM_KERNEL_AUTO = 0, TLBM_KERNEL_FUSED = 1, TLBM_KERNEL_SPLIT = 2 } tlbm_kernel;
+
+/*
+ * Create an engine for an nx x ny x nz lattice and allocate its device memory.
+ *   lattice       TLBM_D2Q9 (nz must be 1) or TLBM_D3Q19.
+ *   kappa[3]      kappa_1..3 > 0 of the free energy (Eq. energy_functional_general
+ *                 with kappa'_m = alpha^2 kappa_m); surface tensions are
+ *                 gamma_mn = alpha (kappa_m + kappa_n)/6 (Eq. SurfTens).
+ *   alpha         interface width > 0.
+ *   tau_f         relaxation time of f (> 1/2), viscosity (tau_f - 1/2)/3.
+ *   M_phi, M_psi  mobilities > 0 of the Cahn-Hilliard equations.
+ *   h[3]          wetting parameters h_1..3 (Eq. Cahn); may be NULL for zeros.
+ *                 Each must satisfy |4 h_m / (alpha kappa_m)| < 1.
+ *   solid_mask    host array of nx*ny*nz bytes, nonzero = solid; copied.  NULL =
+ *                 no solid nodes.
+ *   precision     see tlbm_precision.
+ *   cuda_stream   a cudaStream_t (as void*), or NULL for the default stream.
+ * On success *out is a new handle; populations are zero until tlbm_init_fields or
+ * tlbm_set_populations.  On failure *out is NULL and the status says why.
+ */
+tlbm_status tlbm_create(tlbm **out, tlbm_lattice lattice, int nx, int ny, int nz,
+                        const double kappa[3], double alpha, double tau_f,
+                        double M_phi, double M_psi, const double h[3],
+                        const uint8_t *solid_mask, tlbm_precision precision,
+                        void *cuda_stream);
+
+/* Free all device memory of the handle (NULL is ignored). */
+void tlbm_destroy(tlbm *t);
+
+/* Set Gamma_phi, Gamma_psi (> 0) of the g/k equilibria; tau_phi and tau_psi are
+ * recomputed from the mobilities (Eqs. Mobility1, Mobility2). */
+tlbm_status tlbm_set_gamma(tlbm *t, double gamma_phi, double gamma_psi);
+
+/* Choose the step implementation (see tlbm_kernel). */
+tlbm_status tlbm_set_kernel(tlbm *t, tlbm_kernel kind);
+
+/* Which implementation tlbm_step uses now (resolves AUTO). */
+tlbm_kernel tlbm_get_kernel(const tlbm *t);
+
+/* Tile of the fused step: variant 0 = default, D3Q19 1 = 32x8, 2 = 64x4,
+ * 3 = 16x16 nodes per block; D2Q9 1 = 128, 2 = 256, 3 = 64 nodes per row.
+ * chunk = planes marched per block (0 = chosen from the lattice size).
+ * Results do not depend on the tile. */
+tlbm_status tlbm_set_tile(tlbm *t, int variant, int chunk);
+
+/*
+ * Set the populations to the equilibria of the given fields.
+ *   rho, phi, psi  host double arrays of N = nx*ny*nz values (values on solid
+ *                  nodes are ignored);
+ *   ux, uy, uz     host double velocity arrays, or NULL for zero.
+ * The equilibria use the same derivative stencils and wetting ghosts as a step.
+ * Synchronises the stream.
+ */
+tlbm_status tlbm_init_fields(tlbm *t, const double *rho, const double *phi, const double *psi,
+                             const double *ux, const double *uy, const double *uz);
+
+/* Advance nsteps >= 0 time steps.  Queued on the stream; returns without waiting. */
+tlbm_status tlbm_step(tlbm *t, int64_t nsteps);
+
+/* Number of steps taken since the last init/set of the populations. */
+int64_t tlbm_steps_done(const tlbm *t);
+
+/* Timing mode (on != 0): every step records CUDA events on the stream around
+ * its main kernel(s) (not the final mass reduction) and waits for them, adding
+ * their elapsed time to a total.  Turning it on or off resets the total.  The
+ * waits make tlbm_step synchronous; the kernels themselves are unchanged. */
+tlbm_status tlbm_set_timing(tlbm *t, int on);
+
+/* Total main-kernel milliseconds and number of steps timed since timing was set. */
+tlbm_status tlbm_kernel_time(const tlbm *t, double *ms_total, int64_t *steps);
+
+/*
+ * Copy out macroscopic fields of the current state (host double arrays of N
+ * values; u is [3][N]).  Any pointer may be NULL to skip that field.  Solid
+ * nodes read 0.  Synchronises the stream.
+ */
+tlbm_status tlbm_fields(tlbm *t, double *C1, double *C2, double *C3, double *rho, double *u);
+
+/*
+ * FP64 totals (sum rho, sum phi, sum psi) over fluid nodes of the current state,
+ * reduced in a fixed order (bitwise repeatable).  Returns TLBM_ERR_NONFINITE (and
+ * still writes out) if a total is not finite.  Synchronises the stream.
+ */
+tlbm_status tlbm_mass(tlbm *t, double out[3]);
+
+/*
+ * Totals of the state at the start of the most recent step, as accumulated
+ * inside that step (NaN before the first step), and the non-finite flag of all
+ * steps since the last init.  Synchronises the stream.
+ */
+tlbm_status tlbm_step_mass(tlbm *t, double out[3]);
+
+/*
+ * Conventional populations f_i(r,t), g_i, k_i of the box [x0,x0+bx) x [y0,y0+by)
+ * x [z0,z0+bz) (coordinates wrap periodically) as doubles laid out
+ * [set][i][bz][by][bx].  host must hold 3*Q*bx*by*bz doubles.  Synchronises.
+ */
+tlbm_status tlbm_get_populations_box(tlbm *t, int x0, int y0, int z0, int bx, int by, int bz,
+                                     double *host);
+
+/* Whole-lattice form of tlbm_get_populations_box (3*Q*N doubles). */
+tlbm_status tlbm_get_populations(tlbm *t, double *host);
+
+/* Replace the state by conventional populations (3*Q*N doubles, values on solid
+ * nodes ignored), rounded to the storage precision.  Synchronises. */
+tlbm_status tlbm_set_populations(tlbm *t, const double *host);
+
+/* Bytes of the raw device state (checkpoint size). */
+size_t tlbm_state_bytes(const tlbm *t);
+
+/* Copy the raw device state to / from host memory of tlbm_state_bytes bytes.
+ * A state saved by tlbm_get_state resumes bitwise identically.  Synchronises. */
+tlbm_status tlbm_get_state(tlbm *t, void *host, size_t bytes);
+tlbm_status tlbm_set_state(tlbm *t, const void *host, size_t bytes);
+
+/* Kernel launches per tlbm_step(1) of the current configuration. */
+int tlbm_launches_per_step(const tlbm *t);
+
+/* Message of the last failed call on this handle ("" if none; never NULL). */
+const char *tlbm_last_error(const tlbm *t);
+
+/* Name of a status code. */
+const char *tlbm_status_string(tlbm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TLBM_H */

@@ -1,0 +1,466 @@
+// tlbm_api.cu -- the C ABI declared in include/tlbm.h: parameter checks,
+// device memory, host<->device copies, and dispatch to the kernel tables of
+// each storage format.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/tlbm.h"
+#include "tlbm_internal.h"
+
+using tlbm_host::DevState;
+using tlbm_host::Ops;
+
+struct tlbm {
+    DevState d;
+    const Ops* ops;
+    cudaStream_t st;
+    int device;
+    int kind_req;          // tlbm_kernel requested
+    int64_t steps;
+    double kappa[3], alpha, tau_f, M_phi, M_psi, gamma[2], h[3];
+    size_t esize;          // bytes per stored population
+    size_t tsize;          // bytes per compute value
+    double* staging;       // device doubles for init/fields (8 N), allocated on demand
+    size_t partials_len;   // doubles in d.partials
+    cudaEvent_t ev[2];     // kernel timing events (timing mode)
+    int timing;            // 1: time the main kernel(s) of every step
+    double kernel_ms;      // accumulated main-kernel time in timing mode
+    int64_t kernel_steps;  // steps accumulated in kernel_ms
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+tlbm_status fail(tlbm* t, tlbm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (t) t->err = buf;
+    else g_create_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(t, e_ == cudaErrorMemoryAllocation ? TLBM_ERR_OOM : TLBM_ERR_CUDA,      \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                      \
+    } while (0)
+
+void set_phys(tlbm* t) {
+    auto& p = t->d.phys;
+    const double k1 = t->kappa[0], k2 = t->kappa[1], k3 = t->kappa[2];
+    for (int m = 0; m < 3; ++m) p.kappa[m] = t->kappa[m];
+    p.a2 = t->alpha * t->alpha;
+    p.omega[0] = 1.0 / t->tau_f;
+    p.omega[1] = 1.0 / (0.5 + t->M_phi / t->gamma[0]);
+    p.omega[2] = 1.0 / (0.5 + t->M_psi / t->gamma[1]);
+    p.gamma[0] = t->gamma[0];
+    p.gamma[1] = t->gamma[1];
+    // wall-normal gradients of rho, phi, psi (wetting conditions on the auxiliary fields)
+    const double q1 = t->h[0] / (p.a2 * k1), q2 = t->h[1] / (p.a2 * k2), q3 = t->h[2] / (p.a2 * k3);
+    p.Gw[0] = -q1 - q2 - q3;
+    p.Gw[1] = -q1 + q2;
+    p.Gw[2] = -q3;
+    // mixing coefficients of the pressure tensor
+    p.K[0][0] = (k1 + k2) / 4.0;
+    p.K[1][1] = (k1 + k2) / 4.0;
+    p.K[2][2] = (k1 + k2 + 4.0 * k3) / 4.0;
+    p.K[0][1] = p.K[1][0] = (k1 - k2) / 4.0;
+    p.K[1][2] = p.K[2][1] = -(k1 - k2) / 4.0;
+    p.K[0][2] = p.K[2][0] = -(k1 + k2) / 4.0;
+}
+
+int resolve_kind(const tlbm* t) {
+    if (t->kind_req == TLBM_KERNEL_SPLIT) return tlbm_host::KIND_SPLIT;
+    if (t->kind_req == TLBM_KERNEL_FUSED) return tlbm_host::KIND_FUSED;
+    return t->ops->has_fused(t->d) ? tlbm_host::KIND_FUSED : tlbm_host::KIND_SPLIT;
+}
+
+tlbm_status ensure_staging(tlbm* t) {
+    if (t->staging) return TLBM_OK;
+    CK(cudaMalloc(&t->staging, sizeof(double) * 8 * (size_t)t->d.N));
+    return TLBM_OK;
+}
+
+tlbm_status ensure_mom(tlbm* t) {
+    if (t->d.mom) return TLBM_OK;
+    CK(cudaMalloc(&t->d.mom, t->tsize * 3 * (size_t)t->d.Np));
+    return TLBM_OK;
+}
+
+}  // namespace
+
+namespace tlbm_host {
+int mass_blocks() { return 1216; }
+}  // namespace tlbm_host
+
+extern "C" {
+
+const char* tlbm_status_string(tlbm_status s) {
+    switch (s) {
+        case TLBM_OK: return "TLBM_OK";
+        case TLBM_ERR_ARG: return "TLBM_ERR_ARG";
+        case TLBM_ERR_PARAM: return "TLBM_ERR_PARAM";
+        case TLBM_ERR_CUDA: return "TLBM_ERR_CUDA";
+        case TLBM_ERR_OOM: return "TLBM_ERR_OOM";
+        case TLBM_ERR_NONFINITE: return "TLBM_ERR_NONFINITE";
+        case TLBM_ERR_TIMEOUT: return "TLBM_ERR_TIMEOUT";
+        case TLBM_ERR_UNSUPPORTED: return "TLBM_ERR_UNSUPPORTED";
+    }
+    return "TLBM_ERR_UNKNOWN";
+}
+
+const char* tlbm_last_error(const tlbm* t) {
+    if (!t) return g_create_err.c_str();
+    return t->err.c_str();
+}
+
+void tlbm_destroy(tlbm* t) {
+    if (!t) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(t->device);
+    if (t->st) cudaStreamSynchronize(t->st);
+    else cudaDeviceSynchronize();
+    cudaFree(t->d.pop[0]);
+    cudaFree(t->d.pop[1]);
+    cudaFree((void*)t->d.solid);
+    cudaFree(t->d.mom);
+    cudaFree(t->d.partials);
+    cudaFree(t->d.step_mass);
+    cudaFree(t->d.mass_tmp);
+    cudaFree(t->d.flag);
+    cudaFree(t->staging);
+    if (t->ev[0]) cudaEventDestroy(t->ev[0]);
+    if (t->ev[1]) cudaEventDestroy(t->ev[1]);
+    if (prev >= 0) cudaSetDevice(prev);
+    delete t;
+}
+
+tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz, const double kappa[3],
+                        double alpha, double tau_f, double M_phi, double M_psi, const double h[3],
+                        const uint8_t* solid_mask, tlbm_precision precision, void* cuda_stream) {
+    tlbm* t = nullptr;
+    g_create_err.clear();
+    if (!out) return fail(nullptr, TLBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (lattice != TLBM_D2Q9 && lattice != TLBM_D3Q19)
+        return fail(nullptr, TLBM_ERR_ARG, "lattice must be TLBM_D2Q9 or TLBM_D3Q19");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, TLBM_ERR_ARG, "sizes must be >= 1");
+    if (lattice == TLBM_D2Q9 && nz != 1) return fail(nullptr, TLBM_ERR_ARG, "D2Q9 needs nz == 1");
+    if (!kappa) return fail(nullptr, TLBM_ERR_ARG, "kappa is NULL");
+    const long long N = (long long)nx * ny * nz;
+    if (N > (1LL << 40)) return fail(nullptr, TLBM_ERR_ARG, "lattice too large");
+    double hh[3] = {0, 0, 0};
+    if (h) for (int m = 0; m < 3; ++m) hh[m] = h[m];
+    if (!(alpha > 0) || !std::isfinite(alpha)) return fail(nullptr, TLBM_ERR_PARAM, "alpha must be > 0");
+    for (int m = 0; m < 3; ++m) {
+        if (!(kappa[m] > 0) || !std::isfinite(kappa[m]))
+            return fail(nullptr, TLBM_ERR_PARAM, "kappa_%d must be > 0", m + 1);
+        if (!std::isfinite(hh[m]) || !(std::fabs(4.0 * hh[m] / (alpha * kappa[m])) < 1.0))
+            return fail(nullptr, TLBM_ERR_PARAM, "|4 h_%d / (alpha kappa_%d)| must be < 1", m + 1, m + 1);
+    }
+    if (!(tau_f > 0.5) || !std::isfinite(tau_f)) return fail(nullptr, TLBM_ERR_PARAM, "tau_f must be > 1/2");
+    if (!(M_phi > 0) || !(M_psi > 0) || !std::isfinite(M_phi) || !std::isfinite(M_psi))
+        return fail(nullptr, TLBM_ERR_PARAM, "mobilities must be > 0");
+    const Ops* ops = nullptr;
+    size_t esize = 0, tsize = 0;
+    switch (precision) {
+        case TLBM_FP64: ops = tlbm_host::ops_fp64(lattice); esize = 8; tsize = 8; break;
+        case TLBM_FP32: ops = tlbm_host::ops_fp32(lattice); esize = 4; tsize = 4; break;
+        case TLBM_FP16_OFFSET: ops = tlbm_host::ops_fp16(lattice); esize = 2; tsize = 4; break;
+        case TLBM_BF16_OFFSET: ops = tlbm_host::ops_bf16(lattice); esize = 2; tsize = 4; break;
+        default: return fail(nullptr, TLBM_ERR_ARG, "unknown precision");
+    }
+    if (!ops) return fail(nullptr, TLBM_ERR_UNSUPPORTED, "precision/lattice combination not built");
+
+    t = new tlbm();
+    memset(&t->d, 0, sizeof t->d);
+    t->ops = ops;
+    t->st = static_cast<cudaStream_t>(cuda_stream);
+    t->kind_req = TLBM_KERNEL_AUTO;
+    t->steps = 0;
+    for (int m = 0; m < 3; ++m) { t->kappa[m] = kappa[m]; t->h[m] = hh[m]; }
+    t->alpha = alpha; t->tau_f = tau_f; t->M_phi = M_phi; t->M_psi = M_psi;
+    t->gamma[0] = t->gamma[1] = 1.0;
+    t->esize = esize; t->tsize = tsize;
+    t->staging = nullptr;
+    t->ev[0] = t->ev[1] = nullptr;
+    t->timing = 0;
+    t->kernel_ms = 0.0;
+    t->kernel_steps = 0;
+    cudaGetDevice(&t->device);
+    DevState& d = t->d;
+    d.Q = (int)lattice; d.prec = (int)precision;
+    d.nx = nx; d.ny = ny; d.nz = nz; d.N = N;
+    d.Np = (N + 63) / 64 * 64;
+    d.cur = 0;
+    d.tile = 0;
+    set_phys(t);
+
+    auto bail = [&](tlbm_status s) {
+        g_create_err = t->err;
+        tlbm_destroy(t);
+        return s;
+    };
+    const size_t popbytes = esize * 3 * (size_t)d.Q * (size_t)d.Np;
+    for (int b = 0; b < 2; ++b) {
+        cudaError_t e = cudaMalloc(&d.pop[b], popbytes);
+        if (e != cudaSuccess)
+            return bail(fail(t, TLBM_ERR_OOM, "cudaMalloc(%zu bytes) for populations: %s", popbytes,
+                             cudaGetErrorString(e)));
+        e = cudaMemsetAsync(d.pop[b], 0, popbytes, t->st);
+        if (e != cudaSuccess) return bail(fail(t, TLBM_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e)));
+    }
+    bool any_solid = false;
+    if (solid_mask)
+        for (long long r = 0; r < N && !any_solid; ++r) any_solid = solid_mask[r] != 0;
+    if (any_solid) {
+        uint8_t* ds = nullptr;
+        cudaError_t e = cudaMalloc(&ds, (size_t)N);
+        if (e != cudaSuccess) return bail(fail(t, TLBM_ERR_OOM, "cudaMalloc(mask): %s", cudaGetErrorString(e)));
+        d.solid = ds;
+        e = cudaMemcpy(ds, solid_mask, (size_t)N, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(fail(t, TLBM_ERR_CUDA, "cudaMemcpy(mask): %s", cudaGetErrorString(e)));
+    }
+    // mass partials: step partials (up to one per fused block) + tlbm_mass partials
+    long long nblk = 0;
+    {
+        // generous bound on fused blocks: one per 64 nodes
+        nblk = N / 64 + 1;
+        if (nblk < tlbm_host::mass_blocks()) nblk = tlbm_host::mass_blocks();
+    }
+    t->partials_len = 3 * (size_t)(nblk + tlbm_host::mass_blocks());
+    d.partials_cap = nblk;
+    cudaError_t e = cudaMalloc(&d.partials, sizeof(double) * t->partials_len);
+    if (e == cudaSuccess) e = cudaMalloc(&d.step_mass, sizeof(double) * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&d.mass_tmp, sizeof(double) * 3);
+    if (e == cudaSuccess) e = cudaMalloc(&d.flag, sizeof(int));
+    if (e != cudaSuccess) return bail(fail(t, TLBM_ERR_OOM, "cudaMalloc(reductions): %s", cudaGetErrorString(e)));
+    const double nan3[3] = {NAN, NAN, NAN};
+    e = cudaMemcpy(d.step_mass, nan3, sizeof nan3, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d.flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->st);
+    if (e != cudaSuccess) return bail(fail(t, TLBM_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e)));
+    *out = t;
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_set_gamma(tlbm* t, double gamma_phi, double gamma_psi) {
+    if (!t) return TLBM_ERR_ARG;
+    if (!(gamma_phi > 0) || !(gamma_psi > 0)) return fail(t, TLBM_ERR_PARAM, "Gamma must be > 0");
+    t->gamma[0] = gamma_phi;
+    t->gamma[1] = gamma_psi;
+    set_phys(t);
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_set_kernel(tlbm* t, tlbm_kernel kind) {
+    if (!t) return TLBM_ERR_ARG;
+    if (kind != TLBM_KERNEL_AUTO && kind != TLBM_KERNEL_FUSED && kind != TLBM_KERNEL_SPLIT)
+        return fail(t, TLBM_ERR_ARG, "unknown kernel kind");
+    if (kind == TLBM_KERNEL_FUSED && !t->ops->has_fused(t->d))
+        return fail(t, TLBM_ERR_UNSUPPORTED, "fused step not built for this configuration (solid nodes)");
+    t->kind_req = kind;
+    return TLBM_OK;
+}
+
+tlbm_kernel tlbm_get_kernel(const tlbm* t) {
+    if (!t) return TLBM_KERNEL_AUTO;
+    return resolve_kind(t) == tlbm_host::KIND_FUSED ? TLBM_KERNEL_FUSED : TLBM_KERNEL_SPLIT;
+}
+
+// Tile choice of the fused step: variant (0 = default) and planes per chunk (0 = auto).
+tlbm_status tlbm_set_tile(tlbm* t, int variant, int chunk) {
+    if (!t) return TLBM_ERR_ARG;
+    if (variant < 0 || variant > 3 || chunk < 0 || chunk > 4096) return fail(t, TLBM_ERR_ARG, "bad tile");
+    t->d.tile = variant + 16 * chunk;
+    // partial sums must fit: blocks grow as chunks shrink
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_init_fields(tlbm* t, const double* rho, const double* phi, const double* psi,
+                             const double* ux, const double* uy, const double* uz) {
+    if (!t) return TLBM_ERR_ARG;
+    if (!rho || !phi || !psi) return fail(t, TLBM_ERR_ARG, "rho, phi, psi must not be NULL");
+    tlbm_status s = ensure_staging(t);
+    if (s != TLBM_OK) return s;
+    s = ensure_mom(t);
+    if (s != TLBM_OK) return s;
+    const size_t N = (size_t)t->d.N, nb = N * sizeof(double);
+    double* st = t->staging;
+    CK(cudaMemcpyAsync(st, rho, nb, cudaMemcpyHostToDevice, t->st));
+    CK(cudaMemcpyAsync(st + N, phi, nb, cudaMemcpyHostToDevice, t->st));
+    CK(cudaMemcpyAsync(st + 2 * N, psi, nb, cudaMemcpyHostToDevice, t->st));
+    const double* du = nullptr;
+    if (ux || uy || uz) {
+        double* u = st + 3 * N;
+        if (ux) CK(cudaMemcpyAsync(u, ux, nb, cudaMemcpyHostToDevice, t->st));
+        else CK(cudaMemsetAsync(u, 0, nb, t->st));
+        if (uy) CK(cudaMemcpyAsync(u + N, uy, nb, cudaMemcpyHostToDevice, t->st));
+        else CK(cudaMemsetAsync(u + N, 0, nb, t->st));
+        if (uz) CK(cudaMemcpyAsync(u + 2 * N, uz, nb, cudaMemcpyHostToDevice, t->st));
+        else CK(cudaMemsetAsync(u + 2 * N, 0, nb, t->st));
+        du = u;
+    }
+    CK(t->ops->init(t->d, st, st + N, st + 2 * N, du, t->st));
+    CK(cudaMemsetAsync(t->d.flag, 0, sizeof(int), t->st));
+    CK(cudaStreamSynchronize(t->st));
+    t->steps = 0;
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_step(tlbm* t, int64_t nsteps) {
+    if (!t) return TLBM_ERR_ARG;
+    if (nsteps < 0) return fail(t, TLBM_ERR_ARG, "nsteps must be >= 0");
+    const int kind = resolve_kind(t);
+    if (kind == tlbm_host::KIND_SPLIT) {
+        tlbm_status s = ensure_mom(t);
+        if (s != TLBM_OK) return s;
+    }
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (t->timing) {
+            CK(t->ops->step(t->d, kind, t->st, t->ev[0], t->ev[1]));
+            float ms = 0.0f;
+            CK(cudaEventSynchronize(t->ev[1]));
+            CK(cudaEventElapsedTime(&ms, t->ev[0], t->ev[1]));
+            t->kernel_ms += ms;
+            ++t->kernel_steps;
+        } else {
+            CK(t->ops->step(t->d, kind, t->st, nullptr, nullptr));
+        }
+        ++t->steps;
+    }
+    return TLBM_OK;
+}
+
+int64_t tlbm_steps_done(const tlbm* t) { return t ? t->steps : -1; }
+
+tlbm_status tlbm_set_timing(tlbm* t, int on) {
+    if (!t) return TLBM_ERR_ARG;
+    if (on && !t->ev[0]) {
+        CK(cudaEventCreate(&t->ev[0]));
+        CK(cudaEventCreate(&t->ev[1]));
+    }
+    t->timing = on ? 1 : 0;
+    t->kernel_ms = 0.0;
+    t->kernel_steps = 0;
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_kernel_time(const tlbm* t, double* ms_total, int64_t* steps) {
+    if (!t || !ms_total || !steps) return TLBM_ERR_ARG;
+    *ms_total = t->kernel_ms;
+    *steps = t->kernel_steps;
+    return TLBM_OK;
+}
+
+int tlbm_launches_per_step(const tlbm* t) {
+    if (!t) return -1;
+    return t->ops->launches(t->d, resolve_kind(t));
+}
+
+tlbm_status tlbm_fields(tlbm* t, double* C1, double* C2, double* C3, double* rho, double* u) {
+    if (!t) return TLBM_ERR_ARG;
+    tlbm_status s = ensure_staging(t);
+    if (s != TLBM_OK) return s;
+    const size_t N = (size_t)t->d.N, nb = N * sizeof(double);
+    double* st = t->staging;
+    CK(t->ops->fields(t->d, C1 ? st : nullptr, C2 ? st + N : nullptr, C3 ? st + 2 * N : nullptr,
+                      rho ? st + 3 * N : nullptr, u ? st + 4 * N : nullptr, t->st));
+    if (C1) CK(cudaMemcpyAsync(C1, st, nb, cudaMemcpyDeviceToHost, t->st));
+    if (C2) CK(cudaMemcpyAsync(C2, st + N, nb, cudaMemcpyDeviceToHost, t->st));
+    if (C3) CK(cudaMemcpyAsync(C3, st + 2 * N, nb, cudaMemcpyDeviceToHost, t->st));
+    if (rho) CK(cudaMemcpyAsync(rho, st + 3 * N, nb, cudaMemcpyDeviceToHost, t->st));
+    if (u) CK(cudaMemcpyAsync(u, st + 4 * N, 3 * nb, cudaMemcpyDeviceToHost, t->st));
+    CK(cudaStreamSynchronize(t->st));
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_mass(tlbm* t, double out[3]) {
+    if (!t || !out) return TLBM_ERR_ARG;
+    CK(t->ops->mass(t->d, t->d.mass_tmp, t->st));
+    CK(cudaMemcpyAsync(out, t->d.mass_tmp, 3 * sizeof(double), cudaMemcpyDeviceToHost, t->st));
+    CK(cudaStreamSynchronize(t->st));
+    for (int c = 0; c < 3; ++c)
+        if (!std::isfinite(out[c])) return fail(t, TLBM_ERR_NONFINITE, "mass total %d is not finite", c);
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_step_mass(tlbm* t, double out[3]) {
+    if (!t || !out) return TLBM_ERR_ARG;
+    int flag = 0;
+    CK(cudaMemcpyAsync(out, t->d.step_mass, 3 * sizeof(double), cudaMemcpyDeviceToHost, t->st));
+    CK(cudaMemcpyAsync(&flag, t->d.flag, sizeof(int), cudaMemcpyDeviceToHost, t->st));
+    CK(cudaStreamSynchronize(t->st));
+    if (flag) return fail(t, TLBM_ERR_NONFINITE, "a step produced a non-finite mass total");
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_get_populations_box(tlbm* t, int x0, int y0, int z0, int bx, int by, int bz,
+                                     double* host) {
+    if (!t || !host) return TLBM_ERR_ARG;
+    if (bx < 1 || by < 1 || bz < 1) return fail(t, TLBM_ERR_ARG, "box sizes must be >= 1");
+    const size_t n = 3 * (size_t)t->d.Q * (size_t)bx * by * bz;
+    double* dv = nullptr;
+    CK(cudaMalloc(&dv, n * sizeof(double)));
+    cudaError_t e = t->ops->get_box(t->d, x0, y0, z0, bx, by, bz, dv, t->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, dv, n * sizeof(double), cudaMemcpyDeviceToHost, t->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->st);
+    cudaFree(dv);
+    if (e != cudaSuccess) return fail(t, TLBM_ERR_CUDA, "get_populations_box: %s", cudaGetErrorString(e));
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_get_populations(tlbm* t, double* host) {
+    if (!t) return TLBM_ERR_ARG;
+    return tlbm_get_populations_box(t, 0, 0, 0, t->d.nx, t->d.ny, t->d.nz, host);
+}
+
+tlbm_status tlbm_set_populations(tlbm* t, const double* host) {
+    if (!t || !host) return TLBM_ERR_ARG;
+    const size_t n = 3 * (size_t)t->d.Q * (size_t)t->d.N;
+    double* dv = nullptr;
+    CK(cudaMalloc(&dv, n * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(dv, host, n * sizeof(double), cudaMemcpyHostToDevice, t->st);
+    if (e == cudaSuccess) e = t->ops->set_pops(t->d, dv, t->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->d.flag, 0, sizeof(int), t->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->st);
+    cudaFree(dv);
+    if (e != cudaSuccess) return fail(t, TLBM_ERR_CUDA, "set_populations: %s", cudaGetErrorString(e));
+    t->steps = 0;
+    return TLBM_OK;
+}
+
+size_t tlbm_state_bytes(const tlbm* t) {
+    if (!t) return 0;
+    return t->esize * 3 * (size_t)t->d.Q * (size_t)t->d.Np;
+}
+
+tlbm_status tlbm_get_state(tlbm* t, void* host, size_t bytes) {
+    if (!t || !host) return TLBM_ERR_ARG;
+    if (bytes != tlbm_state_bytes(t)) return fail(t, TLBM_ERR_ARG, "state is %zu bytes", tlbm_state_bytes(t));
+    CK(cudaMemcpyAsync(host, t->d.pop[t->d.cur], bytes, cudaMemcpyDeviceToHost, t->st));
+    CK(cudaStreamSynchronize(t->st));
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_set_state(tlbm* t, const void* host, size_t bytes) {
+    if (!t || !host) return TLBM_ERR_ARG;
+    if (bytes != tlbm_state_bytes(t)) return fail(t, TLBM_ERR_ARG, "state is %zu bytes", tlbm_state_bytes(t));
+    CK(cudaMemcpyAsync(t->d.pop[t->d.cur], host, bytes, cudaMemcpyHostToDevice, t->st));
+    CK(cudaMemsetAsync(t->d.flag, 0, sizeof(int), t->st));
+    CK(cudaStreamSynchronize(t->st));
+    return TLBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// tlbm_internal.h -- host-side structures shared by the C ABI (tlbm_api.cu)
+// and the per-precision kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tlbm_host {
+
+// Physical parameters in double; each translation unit converts to its compute type.
+struct PhysD {
+    double kappa[3];
+    double a2;        // alpha^2
+    double omega[3];  // 1/tau_f, 1/tau_phi, 1/tau_psi
+    double gamma[2];  // Gamma_phi, Gamma_psi
+    double Gw[3];     // wall-normal gradients of rho, phi, psi
+    double K[3][3];   // mixing coefficients kappa_XY
+};
+
+enum Kind { KIND_FUSED = 1, KIND_SPLIT = 2 };
+
+struct DevState {
+    int Q;
+    int prec;            // tlbm_precision
+    int nx, ny, nz;
+    long long N, Np;
+    void* pop[2];        // A-B population buffers, 3*Q*Np elements each
+    int cur;             // buffer holding the current state
+    const uint8_t* solid;  // device mask (nullptr when there are no solid nodes)
+    void* mom;           // split-step moment arrays [3][Np] (compute type); scratch
+    double* partials;    // mass partial sums, 3 per block
+    double* step_mass;   // [3] totals accumulated inside the last step
+    double* mass_tmp;    // [3] totals of tlbm_mass
+    int* flag;           // non-finite flag (int)
+    PhysD phys;
+    int tile;            // fused-kernel tile choice (0 = default)
+    long long partials_cap;  // blocks whose partial sums fit in the first part of partials
+};
+
+struct Ops {
+    // one time step; flips cur.  When ev0/ev1 are not null they are recorded on
+    // the stream just before and just after the step's main kernel(s).
+    cudaError_t (*step)(DevState& d, int kind, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
+    // populations at equilibrium of device double fields (u may be nullptr)
+    cudaError_t (*init)(DevState& d, const double* rho, const double* phi, const double* psi,
+                        const double* u, cudaStream_t st);
+    cudaError_t (*fields)(DevState& d, double* C1, double* C2, double* C3, double* rho, double* u,
+                          cudaStream_t st);
+    cudaError_t (*mass)(DevState& d, double* out, cudaStream_t st);
+    cudaError_t (*get_box)(DevState& d, int x0, int y0, int z0, int bx, int by, int bz, double* out,
+                           cudaStream_t st);
+    cudaError_t (*set_pops)(DevState& d, const double* in, cudaStream_t st);
+    int (*launches)(const DevState& d, int kind);
+    bool (*has_fused)(const DevState& d);
+};
+
+// one table per storage format; nullptr if the lattice is not built
+const Ops* ops_fp64(int Q);
+const Ops* ops_fp32(int Q);
+const Ops* ops_fp16(int Q);
+const Ops* ops_bf16(int Q);
+
+int mass_blocks();
+
+}  // namespace tlbm_host

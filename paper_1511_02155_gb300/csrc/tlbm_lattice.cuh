@@ -1,0 +1,287 @@
+// tlbm_lattice.cuh -- velocity sets, weights, gradient-term tensors, storage
+// formats and the per-node physics of the ternary free-energy LB step
+// (Semprebon, Krueger, Kusumaatmaja, arXiv:1511.02155), for the GPU path.
+//
+// Everything here is compile-time: velocity components and weights are
+// constexpr functions that fold to immediates once the direction loops are
+// unrolled, so no lattice table lives in device memory.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tlbm_dev {
+
+// ------------------------------------------------------------------ lattices
+
+template <int Q>
+struct Lat;
+
+// D2Q9: rest, axis directions 1-4, diagonals 5-8 (opposites adjacent).
+template <>
+struct Lat<9> {
+    static constexpr int D = 2;
+    static constexpr int NAXIS = 4;
+    __host__ __device__ static constexpr int cx(int i) {
+        constexpr int v[9] = {0, 1, -1, 0, 0, 1, -1, -1, 1};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        constexpr int v[9] = {0, 0, 0, 1, -1, 1, -1, 1, -1};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cz(int) { return 0; }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+// D3Q19 in the order the paper's weight table implies: rest; +-x, +-y, +-z;
+// xy-plane edges 7-10; yz-plane edges 11-14; zx-plane edges 15-18.
+template <>
+struct Lat<19> {
+    static constexpr int D = 3;
+    static constexpr int NAXIS = 6;
+    __host__ __device__ static constexpr int cx(int i) {
+        constexpr int v[19] = {0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, 1, -1, -1};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        constexpr int v[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, 1, -1, 1, 1, -1, -1, 0, 0, 0, 0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr int cz(int i) {
+        constexpr int v[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+template <int Q>
+__host__ __device__ constexpr int comp(int i, int a) {
+    return a == 0 ? Lat<Q>::cx(i) : (a == 1 ? Lat<Q>::cy(i) : Lat<Q>::cz(i));
+}
+
+template <int Q>
+__host__ __device__ constexpr int opp(int i) {
+    for (int j = 0; j < Q; ++j)
+        if (Lat<Q>::cx(j) == -Lat<Q>::cx(i) && Lat<Q>::cy(j) == -Lat<Q>::cy(i) &&
+            Lat<Q>::cz(j) == -Lat<Q>::cz(i))
+            return j;
+    return -1;
+}
+
+template <int Q>
+__host__ __device__ constexpr int speed2(int i) {
+    return Lat<Q>::cx(i) * Lat<Q>::cx(i) + Lat<Q>::cy(i) * Lat<Q>::cy(i) +
+           Lat<Q>::cz(i) * Lat<Q>::cz(i);
+}
+
+// Gradient-term tensor w_i^{ab}, component c in (xx, yy, zz, xy, yz, zx).
+// The pressure tensor needs (1/c_s^2) sum_i w_i^{aa} e_ia^2 = 1/2,
+// (1/c_s^2) sum_i w_i^{aa} e_ib^2 = -1/2 and (1/c_s^2) sum_i w_i^{ab} e_ia e_ib = 1.
+// D3Q19 (paper's table): an axis link along a has w^{aa} = 5/36 and -1/9 on the
+// other diagonal components; an edge in plane (a,b) has w^{aa} = w^{bb} = -1/72,
+// 1/36 on the normal component and w^{ab} = e_a e_b / 12.
+// D2Q9 (same normalisation): axis link w^{aa} = 1/9, w^{bb} = -1/18; diagonal
+// link w^{xx} = w^{yy} = -1/72, w^{xy} = e_x e_y / 12.
+template <int Q>
+__host__ __device__ constexpr double tens(int i, int c) {
+    if (i == 0) return 0.0;
+    if (c < 3) {
+        const int ea = comp<Q>(i, c);
+        if (Lat<Q>::D == 2 && c == 2) return 0.0;
+        if (speed2<Q>(i) == 1) {
+            if (Lat<Q>::D == 2) return ea != 0 ? 1.0 / 9.0 : -1.0 / 18.0;
+            return ea != 0 ? 5.0 / 36.0 : -1.0 / 9.0;
+        }
+        // diagonal / edge link
+        if (Lat<Q>::D == 2) return -1.0 / 72.0;
+        return ea != 0 ? -1.0 / 72.0 : 1.0 / 36.0;
+    }
+    const int a = c - 3, b = (c - 3 + 1) % 3;  // xy, yz, zx
+    if (speed2<Q>(i) != 2) return 0.0;
+    return comp<Q>(i, a) * comp<Q>(i, b) / 12.0;
+}
+
+// ------------------------------------------------------------------ storage
+
+// Population storage formats.  Plain float/double store the value; the 16-bit
+// formats store the offset from the rest state (w_i for f at rho_0 = 1, zero
+// for g and k) and compute in float.
+template <typename S>
+struct Store;
+
+template <>
+struct Store<double> {
+    using T = double;
+    static __device__ __forceinline__ double ld(const double* p, long long o, double) { return p[o]; }
+    static __device__ __forceinline__ void st(double* p, long long o, double v, double) { p[o] = v; }
+};
+
+template <>
+struct Store<float> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const float* p, long long o, float) { return p[o]; }
+    static __device__ __forceinline__ void st(float* p, long long o, float v, float) { p[o] = v; }
+};
+
+template <>
+struct Store<__half> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const __half* p, long long o, float off) {
+        return __half2float(p[o]) + off;
+    }
+    static __device__ __forceinline__ void st(__half* p, long long o, float v, float off) {
+        p[o] = __float2half_rn(v - off);
+    }
+};
+
+template <>
+struct Store<__nv_bfloat16> {
+    using T = float;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, long long o, float off) {
+        return __bfloat162float(p[o]) + off;
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, long long o, float v, float off) {
+        p[o] = __float2bfloat16_rn(v - off);
+    }
+};
+
+// rest-state offset of direction i of set s (only used by the offset formats)
+template <int Q, typename S>
+__host__ __device__ constexpr double rest_offset(int s, int i) {
+    return (sizeof(S) == 2 && s == 0) ? Lat<Q>::w(i) : 0.0;
+}
+
+// ------------------------------------------------------------------ geometry
+
+struct Geom {
+    int nx, ny, nz;
+    long long N;   // nodes
+    long long Np;  // stride between direction arrays (N rounded up to 64)
+};
+
+__device__ __forceinline__ int wrap(int v, int n) {
+    v += (v < 0) ? n : 0;
+    v -= (v >= n) ? n : 0;
+    return v;
+}
+
+__device__ __forceinline__ long long node(const Geom& g, int x, int y, int z) {
+    return (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * (long long)z);
+}
+
+// --------------------------------------------------------------- parameters
+
+template <typename T>
+struct Phys {
+    T kappa[3];  // kappa_1..3
+    T a2;        // alpha^2
+    T omega[3];  // 1/tau for f, g, k
+    T gamma[2];  // Gamma_phi, Gamma_psi
+    T Gw[3];     // wall-normal gradients of rho, phi, psi (wetting condition)
+    T K[3][3];   // mixing coefficients kappa_XY of the pressure tensor
+};
+
+// ------------------------------------------------------------- node physics
+
+// Per-node quantities from which every equilibrium population follows:
+//   f_eq_i = w_i (bf + 3 e_i.j + 9/2 rho (e_i.u)^2) + sum_c w_i^c Gs_c
+//   g_eq_i = w_i (bg + 3 phi e_i.u + 9/2 phi (e_i.u)^2)       (k_eq likewise)
+// with bf = 3 p_b - 3 alpha^2 L - 3/2 rho u^2, bg = 3 Gamma_phi mu_phi - 3/2 phi u^2,
+// bk = 3 Gamma_psi mu_psi - 3/2 psi u^2 and Gs_c = 3 alpha^2 G_c (c_s^2 = 1/3).
+template <int Q, typename T>
+struct NodeEq {
+    T rho, phi, psi;
+    T ux, uy, uz;
+    T bf, bg, bk;
+    T Gs[6];
+
+    // X = (rho, phi, psi), j = rho u, grad[X][a], lap[X]
+    __device__ __forceinline__ void setup(const Phys<T>& P, T rho_, T jx, T jy, T jz, T phi_,
+                                          T psi_, const T (&grad)[3][3], const T (&lap)[3]) {
+        rho = rho_; phi = phi_; psi = psi_;
+        const T inv = T(1) / rho;
+        ux = jx * inv; uy = jy * inv; uz = jz * inv;
+        const T uu = ux * ux + uy * uy + uz * uz;
+        // concentrations and their Laplacians (Sec. Auxiliary variables)
+        const T C[3] = {(rho + phi - psi) * T(0.5), (rho - phi - psi) * T(0.5), psi};
+        const T lC[3] = {(lap[0] + lap[1] - lap[2]) * T(0.5), (lap[0] - lap[1] - lap[2]) * T(0.5),
+                         lap[2]};
+        T mu[3];
+        T pb = rho * T(1.0 / 3.0);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const T c = C[m];
+            const T c1 = T(1) - c;
+            mu[m] = P.kappa[m] * (c * c1 * (T(1) - T(2) * c) - P.a2 * lC[m]);
+            pb += P.kappa[m] * T(0.5) * c * c * c1 * (T(1) - T(3) * c);
+        }
+        const T mu_phi = (mu[0] - mu[1]) * T(0.5);
+        const T mu_psi = mu[2] - (mu[0] + mu[1]) * T(0.5);
+        // Laplacian part of the pressure tensor: L = sum_XY K_XY X lap Y
+        const T X[3] = {rho, phi, psi};
+        T Lp = T(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            T s = T(0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) s += P.K[a][b] * lap[b];
+            Lp += X[a] * s;
+        }
+        bf = T(3) * pb - T(3) * P.a2 * Lp - T(1.5) * rho * uu;
+        bg = T(3) * P.gamma[0] * mu_phi - T(1.5) * phi * uu;
+        bk = T(3) * P.gamma[1] * mu_psi - T(1.5) * psi * uu;
+        // gradient part: G_ab = v_a^T K v_b with v_a = (d_a rho, d_a phi, d_a psi)
+        constexpr int D = Lat<Q>::D;
+        T Kv[3][3];  // [b][X] = (K v_b)_X
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+#pragma unroll
+            for (int x = 0; x < 3; ++x)
+                Kv[b][x] = P.K[x][0] * grad[0][b] + P.K[x][1] * grad[1][b] + P.K[x][2] * grad[2][b];
+        const T s3 = T(3) * P.a2;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const int a = c < 3 ? c : c - 3;
+            const int b = c < 3 ? c : (c - 3 + 1) % 3;
+            if (a < D && b < D)
+                Gs[c] = s3 * (grad[0][a] * Kv[b][0] + grad[1][a] * Kv[b][1] + grad[2][a] * Kv[b][2]);
+            else
+                Gs[c] = T(0);
+        }
+    }
+
+    __device__ __forceinline__ T eu(int i) const {
+        T s = T(0);
+        if (Lat<Q>::cx(i)) s += T(Lat<Q>::cx(i)) * ux;
+        if (Lat<Q>::cy(i)) s += T(Lat<Q>::cy(i)) * uy;
+        if (Lat<Q>::cz(i)) s += T(Lat<Q>::cz(i)) * uz;
+        return s;
+    }
+
+    __device__ __forceinline__ T grad_term(int i) const {
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            if (tens<Q>(i, c) != 0.0) s += T(tens<Q>(i, c)) * Gs[c];
+        return s;
+    }
+
+    // equilibria of direction i >= 1
+    __device__ __forceinline__ void eq(int i, T& fe, T& ge, T& ke) const {
+        const T w = T(Lat<Q>::w(i));
+        const T e = eu(i);
+        const T e2 = T(4.5) * e * e;
+        fe = w * (bf + rho * (T(3) * e + e2)) + grad_term(i);
+        ge = w * (bg + phi * (T(3) * e + e2));
+        ke = w * (bk + psi * (T(3) * e + e2));
+    }
+};
+
+}  // namespace tlbm_dev

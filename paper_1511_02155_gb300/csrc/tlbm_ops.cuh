@@ -1,0 +1,152 @@
+// tlbm_ops.cuh -- launch table of one storage format: turns the ABI's device
+// state into kernel launches.  Included once per precision translation unit.
+#pragma once
+
+#include "tlbm_fused.cuh"
+#include "tlbm_kernels.cuh"
+
+namespace tlbm_dev {
+
+using tlbm_host::DevState;
+using tlbm_host::PhysD;
+
+template <typename T>
+inline Phys<T> to_phys(const PhysD& p) {
+    Phys<T> q;
+    for (int m = 0; m < 3; ++m) {
+        q.kappa[m] = T(p.kappa[m]);
+        q.omega[m] = T(p.omega[m]);
+        q.Gw[m] = T(p.Gw[m]);
+        for (int n = 0; n < 3; ++n) q.K[m][n] = T(p.K[m][n]);
+    }
+    q.a2 = T(p.a2);
+    q.gamma[0] = T(p.gamma[0]);
+    q.gamma[1] = T(p.gamma[1]);
+    return q;
+}
+
+inline Geom geom(const DevState& d) { return Geom{d.nx, d.ny, d.nz, d.N, d.Np}; }
+
+inline int grid_for(long long n) {
+    long long b = (n + kThreads - 1) / kThreads;
+    const long long cap = 152LL * 8;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <int Q, typename S>
+struct Impl {
+    using T = typename Store<S>::T;
+
+    template <bool SOLID>
+    static void split(DevState& d, cudaStream_t st) {
+        const Geom g = geom(d);
+        const Phys<T> P = to_phys<T>(d.phys);
+        const S* src = static_cast<const S*>(d.pop[d.cur]);
+        S* dst = static_cast<S*>(d.pop[1 - d.cur]);
+        T* mom = static_cast<T*>(d.mom);
+        const int grid = grid_for(g.N);
+        k_moments<Q, S, SOLID, true><<<kMassBlocks, kThreads, 0, st>>>(g, src, d.solid, mom, d.partials);
+        if (SOLID) k_ghosts<Q, T><<<grid, kThreads, 0, st>>>(g, d.solid, mom, P);
+        k_collide_split<Q, S, SOLID><<<grid, kThreads, 0, st>>>(g, src, dst, d.solid, mom, P);
+    }
+
+    static cudaError_t step(DevState& d, int kind, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+        if (ev0) cudaEventRecord(ev0, st);
+        if (kind == tlbm_host::KIND_FUSED) {
+            cudaError_t e = fused_step<Q, S>(d, to_phys<T>(d.phys), st);
+            if (e != cudaSuccess) return e;
+        } else {
+            if (d.solid) split<true>(d, st);
+            else split<false>(d, st);
+        }
+        if (ev1) cudaEventRecord(ev1, st);
+        k_mass_final<<<1, kThreads, 0, st>>>(d.partials, fused_partials<Q, S>(d, kind), d.step_mass,
+                                             d.flag);
+        d.cur ^= 1;
+        return cudaGetLastError();
+    }
+
+    static cudaError_t init(DevState& d, const double* rho, const double* phi, const double* psi,
+                            const double* u, cudaStream_t st) {
+        const Geom g = geom(d);
+        const Phys<T> P = to_phys<T>(d.phys);
+        T* mom = static_cast<T*>(d.mom);
+        S* dst = static_cast<S*>(d.pop[d.cur]);
+        const int grid = grid_for(g.N);
+        k_fields_to_mom<T><<<grid, kThreads, 0, st>>>(g, rho, phi, psi, d.solid, mom);
+        if (d.solid) {
+            k_ghosts<Q, T><<<grid, kThreads, 0, st>>>(g, d.solid, mom, P);
+            k_init_eq<Q, S, true><<<grid, kThreads, 0, st>>>(g, dst, d.solid, mom, u, P);
+        } else {
+            k_init_eq<Q, S, false><<<grid, kThreads, 0, st>>>(g, dst, d.solid, mom, u, P);
+        }
+        return cudaGetLastError();
+    }
+
+    static cudaError_t fields(DevState& d, double* C1, double* C2, double* C3, double* rho, double* u,
+                              cudaStream_t st) {
+        const Geom g = geom(d);
+        const S* src = static_cast<const S*>(d.pop[d.cur]);
+        const int grid = grid_for(g.N);
+        if (d.solid) k_fields<Q, S, true><<<grid, kThreads, 0, st>>>(g, src, d.solid, C1, C2, C3, rho, u);
+        else k_fields<Q, S, false><<<grid, kThreads, 0, st>>>(g, src, d.solid, C1, C2, C3, rho, u);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t mass(DevState& d, double* out, cudaStream_t st) {
+        const Geom g = geom(d);
+        const S* src = static_cast<const S*>(d.pop[d.cur]);
+        double* part = d.partials + 3 * d.partials_cap;  // after the step partials
+        if (d.solid)
+            k_moments<Q, S, true, false><<<kMassBlocks, kThreads, 0, st>>>(g, src, d.solid, nullptr, part);
+        else
+            k_moments<Q, S, false, false><<<kMassBlocks, kThreads, 0, st>>>(g, src, d.solid, nullptr, part);
+        k_mass_final<<<1, kThreads, 0, st>>>(part, kMassBlocks, out, d.flag);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t get_box(DevState& d, int x0, int y0, int z0, int bx, int by, int bz, double* out,
+                               cudaStream_t st) {
+        const Geom g = geom(d);
+        const S* src = static_cast<const S*>(d.pop[d.cur]);
+        const int grid = grid_for((long long)bx * by * bz);
+        if (d.solid)
+            k_get_box<Q, S, true><<<grid, kThreads, 0, st>>>(g, src, d.solid, x0, y0, z0, bx, by, bz, out);
+        else
+            k_get_box<Q, S, false><<<grid, kThreads, 0, st>>>(g, src, d.solid, x0, y0, z0, bx, by, bz, out);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t set_pops(DevState& d, const double* in, cudaStream_t st) {
+        const Geom g = geom(d);
+        S* dst = static_cast<S*>(d.pop[d.cur]);
+        const int grid = grid_for(g.N);
+        if (d.solid) k_set_pops<Q, S, true><<<grid, kThreads, 0, st>>>(g, in, d.solid, dst);
+        else k_set_pops<Q, S, false><<<grid, kThreads, 0, st>>>(g, in, d.solid, dst);
+        return cudaGetLastError();
+    }
+
+    static int launches(const DevState& d, int kind) {
+        if (kind == tlbm_host::KIND_FUSED) return fused_launches<Q, S>(d) + 1;
+        return (d.solid ? 3 : 2) + 1;
+    }
+
+    static bool has_fused(const DevState& d) { return fused_supported<Q, S>(d); }
+
+    static const tlbm_host::Ops* table() {
+        static const tlbm_host::Ops o = {&step, &init, &fields, &mass, &get_box, &set_pops, &launches,
+                                         &has_fused};
+        return &o;
+    }
+};
+
+}  // namespace tlbm_dev
+
+#define TLBM_DEFINE_OPS(NAME, S)                                   \
+    namespace tlbm_host {                                          \
+    const Ops* NAME(int Q) {                                       \
+        if (Q == 9) return tlbm_dev::Impl<9, S>::table();          \
+        if (Q == 19) return tlbm_dev::Impl<19, S>::table();        \
+        return nullptr;                                            \
+    }                                                              \
+    }
