@@ -38,13 +38,17 @@ METRIC = "MLUPS and % HBM roofline per ternary step (FP32 vs FP16-store) at fixe
 STORE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
 
 
-def workload(name: str):
+def workload(name: str, size: int = 0):
+    """(config dict, label).  size overrides the edge of the spinodal / probe
+    lattices (used for small profiling cases of the same kernel)."""
     if name == "spinodal256":
-        return W.spinodal_3d(256, seed=3), "D3Q19 256^3 periodic ternary spinodal decomposition"
+        n = size or 256
+        return W.spinodal_3d(n, seed=3), f"D3Q19 {n}^3 periodic ternary spinodal decomposition"
     if name == "lens512":
         return W.lens_512x256(), "D2Q9 512x256 periodic liquid lens, radius 60 (L2-resident)"
     if name == "probe8192":
-        return W.probe_2d(8192), "D2Q9 8192^2 periodic ternary spinodal mixture"
+        n = size or 8192
+        return W.probe_2d(n), f"D2Q9 {n}^2 periodic ternary spinodal mixture"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -212,6 +216,21 @@ def run_reference(args, cfg_name, cfg, label):
     print(json.dumps(line), flush=True)
 
 
+def reduce_max(value: float, dist, device="cuda") -> float:
+    """Maximum of a per-rank scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world: int, nodes_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: every rank advances its own lattice `steps` times."""
+    return world * nodes_per_rank * steps / seconds / 1e6
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -222,11 +241,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "split"])
     ap.add_argument("--tile", default="0,0")
+    ap.add_argument("--size", type=int, default=0, help="lattice edge override (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
-    cfg, label = workload(args.workload)
+    cfg, label = workload(args.workload, args.size)
 
     if args.impl == "reference":
         run_reference(args, args.workload, cfg, label)
@@ -281,14 +301,10 @@ def main():
         eng.step(args.steps)
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1), dist)
     clocks = clk.summary()
     m_after = eng.step_mass()  # raises on a non-finite total
-    value = world * N * args.steps / (ms / 1e3) / 1e6
+    value = job_mlups(world, N, args.steps, ms / 1e3)
 
     # main-kernel duration, CUDA events on the engine's stream around each launch
     eng.set_timing(True)
@@ -301,7 +317,7 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     kind = eng.kernel
-    tag = f"{kind}:{args.workload}:{args.precision}"
+    tag = f"{kind}:{args.workload}:{args.precision}:{args.tile}"
     traffic = traffic_from_profiles(tag, kernel_source_digest())
 
     # end to end through the public API with host buffers: upload the fields from
@@ -315,12 +331,8 @@ def main():
     eng.fields_into(*(t.data_ptr() for t in outs))
     _ = eng.mass()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": round(world * N * args.steps / e2e_s / 1e6, 2), "unit": "MLUPS",
+    e2e_s = reduce_max(time.perf_counter() - t0, dist)
+    e2e = {"value": round(job_mlups(world, N, args.steps, e2e_s), 2), "unit": "MLUPS",
            "h2d_bytes_per_step": round(3 * 8 * N / args.steps, 1),
            "d2h_bytes_per_step": round((3 * 8 * N + 24) / args.steps, 1),
            "job": f"upload rho/phi/psi (fp64, pinned) + equilibrium init, {args.steps} steps, "

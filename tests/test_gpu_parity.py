@@ -1,9 +1,12 @@
 """GPU parity: the CUDA step (through the C ABI) against the FP64 CPU oracle.
 
 Tolerances
-- FP64 storage: every field (C_1, C_2, C_3, rho) and every population within a
-  relative 1e-12 of the oracle (relative to the field's largest magnitude)
-  after the stated number of steps; velocities within 1e-14 absolute.
+- FP64 storage: every field (C_1, C_2, C_3, rho) and every population set within
+  a relative 1e-12 of the oracle after the stated number of steps, relative to
+  max(largest magnitude of the field, 1) -- concentrations and densities are
+  O(1) by construction, and a field that is identically zero (a fluid absent
+  from the geometry) is compared on that O(1) scale, not on its rounding
+  noise; velocities within 1e-14 absolute.
 - FP32 storage: max |dC_m| <= 1e-4 against the FP64 oracle.
 - Full-size lattices: the GPU state after T steps is read back in patches;
   the oracle advances each patch one step (periodic wrap inside the patch,
@@ -42,7 +45,7 @@ def _setup(Q, shape, C, precision, kernel="auto", solid=None, kappa=(0.01, 0.02,
 
 
 def _rel(a, b):
-    scale = max(np.abs(b).max(), 1e-300)
+    scale = max(np.abs(b).max(), 1.0)
     return np.abs(a - b).max() / scale
 
 
