@@ -203,6 +203,8 @@ tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz
     d.Q = (int)lattice; d.prec = (int)precision;
     d.nx = nx; d.ny = ny; d.nz = nz; d.N = N;
     d.Np = (N + 63) / 64 * 64;
+    d.ncx = (nx + 31) / 32;
+    d.pop_elems = (long long)ny * nz * d.ncx * 32 * 3 * d.Q;
     d.cur = 0;
     d.tile = 0;
     set_phys(t);
@@ -212,7 +214,7 @@ tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz
         tlbm_destroy(t);
         return s;
     };
-    const size_t popbytes = esize * 3 * (size_t)d.Q * (size_t)d.Np;
+    const size_t popbytes = esize * (size_t)d.pop_elems;
     for (int b = 0; b < 2; ++b) {
         cudaError_t e = cudaMalloc(&d.pop[b], popbytes);
         if (e != cudaSuccess)
@@ -443,7 +445,7 @@ tlbm_status tlbm_set_populations(tlbm* t, const double* host) {
 
 size_t tlbm_state_bytes(const tlbm* t) {
     if (!t) return 0;
-    return t->esize * 3 * (size_t)t->d.Q * (size_t)t->d.Np;
+    return t->esize * (size_t)t->d.pop_elems;
 }
 
 tlbm_status tlbm_get_state(tlbm* t, void* host, size_t bytes) {

@@ -40,15 +40,22 @@ struct Axes {
 
 struct MGeom {
     int NA, NB, NM;       // extents along a, b, m
-    long long plane;      // NA * NB
-    long long Np;         // direction stride
     int MC;               // planes per chunk
     int tilesA, tilesB;   // tiles per plane
+    long long rowstride;  // elements between consecutive (b, m) rows: ncx * 3Q * 32
 };
 
 __device__ __forceinline__ int modp(int v, int n) {
     v %= n;
     return v < 0 ? v + n : v;
+}
+
+// single periodic wrap of v in [-n, 2n)
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+template <int Q>
+__device__ __forceinline__ int xpart(int a) {
+    return (a >> 5) * (3 * Q * 32) + (a & 31);
 }
 
 template <int Q, typename S, int TX, int TY>
@@ -63,10 +70,11 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
     constexpr int HH = TY + 2 * HY;
     constexpr int HN = HW * HH;
     constexpr int NT = TX * TY;
+    constexpr int NBORDER = HN - NT;
     static_assert(D == 3 || TY == 1, "2-D tiles are one row");
+    static_assert(NBORDER <= NT, "one border node per thread at most");
 
     __shared__ T sm[4][3][HN];  // moment ring: rho, phi, psi over tile + halo
-    __shared__ T sj[3][3][NT];  // j ring over the tile
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
@@ -77,148 +85,186 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
     const int A0 = tileA * TX, B0 = tileB * TY;
     const int M0 = chunk * g.MC;
     const int M1 = min(M0 + g.MC, g.NM);
-    const int a = A0 + tx, b = B0 + ty;
-    const bool active = (a < g.NA) && (b < g.NB);
+    const bool active = (A0 + tx < g.NA) && (B0 + ty < g.NB);
 
-    // Phase M: moments of plane m over tile + halo into ring slot `slot`.
-    auto moments_plane = [&](int m, int slot, int jslot) {
-        const int mm = modp(m, g.NM);
-        const long long om[3] = {(long long)modp(mm - 1, g.NM) * g.plane, (long long)mm * g.plane,
-                                 (long long)modp(mm + 1, g.NM) * g.plane};
-        for (int h = tid; h < HN; h += NT) {
-            const int hx = h % HW, hy = h / HW;
-            const int aa = modp(A0 + hx - 1, g.NA);
-            const int bb = (D == 3) ? modp(B0 + hy - HY, g.NB) : 0;
-            const long long oa[3] = {modp(aa - 1, g.NA), aa, modp(aa + 1, g.NA)};
-            const long long ob[3] = {(long long)modp(bb - 1, g.NB) * g.NA, (long long)bb * g.NA,
-                                     (long long)modp(bb + 1, g.NB) * g.NA};
+    // Node 0 of every thread: its own tile slot (coordinates wrap for threads past
+    // the lattice edge, whose slots serve as the periodic halo of active ones).
+    // Node 1: one border slot of the halo ring, for tid < NBORDER.
+    int h[2], xp[2][3], yb[2][3];
+    {
+        int hx[2], hy[2];
+        hx[0] = tx + 1;
+        hy[0] = ty + HY;
+        hx[1] = 0;
+        hy[1] = 0;
+        if (D == 2) {
+            hx[1] = tid == 0 ? 0 : HW - 1;
+        } else if (tid < HW) {
+            hx[1] = tid;
+        } else if (tid < 2 * HW) {
+            hx[1] = tid - HW;
+            hy[1] = HH - 1;
+        } else {
+            const int k = tid - 2 * HW;
+            hx[1] = k < HH - 2 ? 0 : HW - 1;
+            hy[1] = 1 + (k < HH - 2 ? k : k - (HH - 2));
+        }
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+            h[n] = hy[n] * HW + hx[n];
+            const int aa = modp(A0 + hx[n] - 1, g.NA);
+            const int bb = (D == 3) ? modp(B0 + hy[n] - HY, g.NB) : 0;
+            xp[n][0] = xpart<Q>(wrap1(aa - 1, g.NA));
+            xp[n][1] = xpart<Q>(aa);
+            xp[n][2] = xpart<Q>(wrap1(aa + 1, g.NA));
+            yb[n][0] = (D == 3) ? wrap1(bb - 1, g.NB) : 0;
+            yb[n][1] = bb;
+            yb[n][2] = (D == 3) ? wrap1(bb + 1, g.NB) : 0;
+        }
+    }
+    const int nnodes = tid < NBORDER ? 2 : 1;
+
+    // base pointer of the pull source of direction i for node n at plane rows zr
+    auto src_of = [&](int n, const int (&zr)[3], int ca, int cb, int cm) -> const S* {
+        const long long row = (long long)zr[1 - cm] * g.NB + yb[n][1 - cb];
+        return src + row * g.rowstride + xp[n][1 - ca];
+    };
+
+    // Phase M: moments of plane m for this thread's nodes into ring slot `slot`;
+    // node 0's momentum density is returned in j.
+    auto moments_plane = [&](int m, int slot, T (&j)[3]) {
+        const int mm = wrap1(m, g.NM);
+        const int zr[3] = {wrap1(mm - 1, g.NM), mm, wrap1(mm + 1, g.NM)};
+#pragma unroll
+        for (int n = 0; n < 2; ++n) {
+            if (n >= nnodes) break;
             T rho = T(0), ja = T(0), jb = T(0), jm = T(0), phi = T(0), psi = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const long long q = oa[1 - A::ca(i)] + ob[1 - A::cb(i)] + om[1 - A::cm(i)];
-                const T f = Store<S>::ld(src, (long long)(0 * Q + i) * g.Np + q, T(rest_offset<Q, S>(0, i)));
+                const S* p = src_of(n, zr, A::ca(i), A::cb(i), A::cm(i));
+                const T f = Store<S>::ld(p, (0 * Q + i) << 5, T(rest_offset<Q, S>(0, i)));
                 rho += f;
                 if (A::ca(i)) ja += T(A::ca(i)) * f;
                 if (A::cb(i)) jb += T(A::cb(i)) * f;
                 if (A::cm(i)) jm += T(A::cm(i)) * f;
-                phi += Store<S>::ld(src, (long long)(1 * Q + i) * g.Np + q, T(0));
-                psi += Store<S>::ld(src, (long long)(2 * Q + i) * g.Np + q, T(0));
+                phi += Store<S>::ld(p, (1 * Q + i) << 5, T(0));
+                psi += Store<S>::ld(p, (2 * Q + i) << 5, T(0));
             }
-            sm[slot][0][h] = rho;
-            sm[slot][1][h] = phi;
-            sm[slot][2][h] = psi;
-            if (jslot >= 0 && hx >= 1 && hx <= TX && hy >= HY && hy < HY + TY) {
-                const int t = (hy - HY) * TX + (hx - 1);
-                sj[jslot][0][t] = ja;
-                sj[jslot][1][t] = jb;
-                sj[jslot][2][t] = jm;
+            sm[slot][0][h[n]] = rho;
+            sm[slot][1][h[n]] = phi;
+            sm[slot][2][h[n]] = psi;
+            if (n == 0) {
+                j[0] = ja;
+                j[1] = jb;
+                j[2] = jm;
             }
         }
     };
 
     double mr = 0.0, mp = 0.0, ms = 0.0;
+    T jc[3], jn[3];
 
-    moments_plane(M0 - 1, (M0 + 3) & 3, -1);
-    moments_plane(M0, M0 & 3, M0 % 3);
-
-    const long long oa_c[3] = {modp(a - 1, g.NA), a, modp(a + 1, g.NA)};
-    const long long ob_c[3] = {(long long)modp(b - 1, g.NB) * g.NA, (long long)b * g.NA,
-                               (long long)modp(b + 1, g.NB) * g.NA};
+    moments_plane(M0 - 1, (M0 + 3) & 3, jn);
+    moments_plane(M0, M0 & 3, jc);
 
     for (int m = M0; m < M1; ++m) {
-        moments_plane(m + 1, (m + 1) & 3, (m + 1) % 3);
+        moments_plane(m + 1, (m + 1) & 3, jn);
         __syncthreads();
-        if (!active) continue;
-
-        // ---- derivatives from the ring (pairs of opposite links)
-        const int hx0 = tx + 1, hy0 = ty + HY;
-        const int c0 = hy0 * HW + hx0;
-        T X0[3], gA[3], gB[3], gM[3], lp[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            X0[c] = sm[m & 3][c][c0];
-            gA[c] = gB[c] = gM[c] = lp[c] = T(0);
-        }
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            if (opp<Q>(i) < i) continue;
-            const int sp = (m + A::cm(i)) & 3, sn = (m - A::cm(i)) & 3;
-            const int cp = c0 + A::cb(i) * HW + A::ca(i);
-            const int cn = c0 - A::cb(i) * HW - A::ca(i);
-            const T w = T(Lat<Q>::w(i));
+        if (active) {
+            // ---- derivatives from the ring (pairs of opposite links)
+            const int c0 = h[0];
+            T X0[3], gA[3], gB[3], gM[3], lp[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const T xp = sm[sp][c][cp], xn = sm[sn][c][cn];
-                const T d = w * (xp - xn);
-                if (A::ca(i)) gA[c] += T(A::ca(i)) * d;
-                if (A::cb(i)) gB[c] += T(A::cb(i)) * d;
-                if (A::cm(i)) gM[c] += T(A::cm(i)) * d;
-                lp[c] += w * (xp + xn);
+                X0[c] = sm[m & 3][c][c0];
+                gA[c] = gB[c] = gM[c] = lp[c] = T(0);
             }
-        }
-        T grad[3][3], lap[3];
-        constexpr T wrest = T(1.0 - Lat<Q>::w(0));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            lap[c] = T(6) * (lp[c] - wrest * X0[c]);
-            grad[c][0] = T(3) * gA[c];
-            if (D == 3) {
-                grad[c][1] = T(3) * gB[c];
-                grad[c][2] = T(3) * gM[c];
-            } else {
-                grad[c][1] = T(3) * gM[c];
-                grad[c][2] = T(0);
+            for (int i = 1; i < Q; ++i) {
+                if (opp<Q>(i) < i) continue;
+                const int sp = (m + A::cm(i)) & 3, sn = (m - A::cm(i)) & 3;
+                const int cp = c0 + A::cb(i) * HW + A::ca(i);
+                const int cn = c0 - A::cb(i) * HW - A::ca(i);
+                const T w = T(Lat<Q>::w(i));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const T xpv = sm[sp][c][cp], xnv = sm[sn][c][cn];
+                    const T d = w * (xpv - xnv);
+                    if (A::ca(i)) gA[c] += T(A::ca(i)) * d;
+                    if (A::cb(i)) gB[c] += T(A::cb(i)) * d;
+                    if (A::cm(i)) gM[c] += T(A::cm(i)) * d;
+                    lp[c] += w * (xpv + xnv);
+                }
             }
-        }
-        const int t = ty * TX + tx;
-        const int js = m % 3;
-        const T jA = sj[js][0][t], jB = sj[js][1][t], jM = sj[js][2][t];
-        NodeEq<Q, T> E;
-        if (D == 3) E.setup(P, X0[0], jA, jB, jM, X0[1], X0[2], grad, lap);
-        else E.setup(P, X0[0], jA, jM, T(0), X0[1], X0[2], grad, lap);
-        mr += (double)X0[0]; mp += (double)X0[1]; ms += (double)X0[2];
+            T grad[3][3], lap[3];
+            constexpr T wrest = T(1.0 - Lat<Q>::w(0));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                lap[c] = T(6) * (lp[c] - wrest * X0[c]);
+                grad[c][0] = T(3) * gA[c];
+                if (D == 3) {
+                    grad[c][1] = T(3) * gB[c];
+                    grad[c][2] = T(3) * gM[c];
+                } else {
+                    grad[c][1] = T(3) * gM[c];
+                    grad[c][2] = T(0);
+                }
+            }
+            NodeEq<Q, T> E;
+            if (D == 3) E.setup(P, X0[0], jc[0], jc[1], jc[2], X0[1], X0[2], grad, lap);
+            else E.setup(P, X0[0], jc[0], jc[2], T(0), X0[1], X0[2], grad, lap);
+            mr += (double)X0[0];
+            mp += (double)X0[1];
+            ms += (double)X0[2];
 
-        // ---- collide + store, direction pairs
-        const long long om_c[3] = {(long long)modp(m - 1, g.NM) * g.plane, (long long)m * g.plane,
-                                   (long long)modp(m + 1, g.NM) * g.plane};
-        const long long r = oa_c[1] + ob_c[1] + om_c[1];
-        T sf = T(0), sg = T(0), sk = T(0);
+            // ---- collide + store, direction pairs
+            const int zr[3] = {wrap1(m - 1, g.NM), m, wrap1(m + 1, g.NM)};
+            const long long roff = ((long long)m * g.NB + yb[0][1]) * g.rowstride + xp[0][1];
+            S* out = dst + roff;
+            const S* ctr = src + roff;
+            T sf = T(0), sg = T(0), sk = T(0);
 #pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int o = opp<Q>(i);
-            if (o < i) continue;
-            const long long qi = oa_c[1 - A::ca(i)] + ob_c[1 - A::cb(i)] + om_c[1 - A::cm(i)];
-            const long long qo = oa_c[1 + A::ca(i)] + ob_c[1 + A::cb(i)] + om_c[1 + A::cm(i)];
-            const T offi = T(rest_offset<Q, S>(0, i));
-            const T fi = Store<S>::ld(src, (long long)(0 * Q + i) * g.Np + qi, offi);
-            const T fo = Store<S>::ld(src, (long long)(0 * Q + o) * g.Np + qo, offi);
-            const T gi = Store<S>::ld(src, (long long)(1 * Q + i) * g.Np + qi, T(0));
-            const T go = Store<S>::ld(src, (long long)(1 * Q + o) * g.Np + qo, T(0));
-            const T ki = Store<S>::ld(src, (long long)(2 * Q + i) * g.Np + qi, T(0));
-            const T ko = Store<S>::ld(src, (long long)(2 * Q + o) * g.Np + qo, T(0));
-            // equilibria of the pair: even part shared, odd part flips sign
-            const T w = T(Lat<Q>::w(i));
-            const T e = E.eu(i);
-            const T e2 = T(4.5) * e * e;
-            const T gt = E.grad_term(i);
-            const T fev = w * (E.bf + E.rho * e2) + gt, fod = w * T(3) * E.rho * e;
-            const T gev = w * (E.bg + E.phi * e2), god = w * T(3) * E.phi * e;
-            const T kev = w * (E.bk + E.psi * e2), kod = w * T(3) * E.psi * e;
-            sf += T(2) * fev; sg += T(2) * gev; sk += T(2) * kev;
-            Store<S>::st(dst, (long long)(0 * Q + i) * g.Np + r, fi + P.omega[0] * ((fev + fod) - fi), offi);
-            Store<S>::st(dst, (long long)(0 * Q + o) * g.Np + r, fo + P.omega[0] * ((fev - fod) - fo), offi);
-            Store<S>::st(dst, (long long)(1 * Q + i) * g.Np + r, gi + P.omega[1] * ((gev + god) - gi), T(0));
-            Store<S>::st(dst, (long long)(1 * Q + o) * g.Np + r, go + P.omega[1] * ((gev - god) - go), T(0));
-            Store<S>::st(dst, (long long)(2 * Q + i) * g.Np + r, ki + P.omega[2] * ((kev + kod) - ki), T(0));
-            Store<S>::st(dst, (long long)(2 * Q + o) * g.Np + r, ko + P.omega[2] * ((kev - kod) - ko), T(0));
+            for (int i = 1; i < Q; ++i) {
+                const int o = opp<Q>(i);
+                if (o < i) continue;
+                const S* pi = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
+                const S* po = src_of(0, zr, -A::ca(i), -A::cb(i), -A::cm(i));
+                const T offi = T(rest_offset<Q, S>(0, i));
+                const T fi = Store<S>::ld(pi, (0 * Q + i) << 5, offi);
+                const T fo = Store<S>::ld(po, (0 * Q + o) << 5, offi);
+                const T gi = Store<S>::ld(pi, (1 * Q + i) << 5, T(0));
+                const T go = Store<S>::ld(po, (1 * Q + o) << 5, T(0));
+                const T ki = Store<S>::ld(pi, (2 * Q + i) << 5, T(0));
+                const T ko = Store<S>::ld(po, (2 * Q + o) << 5, T(0));
+                // equilibria of the pair: even part shared, odd part flips sign
+                const T w = T(Lat<Q>::w(i));
+                const T e = E.eu(i);
+                const T e2 = T(4.5) * e * e;
+                const T gt = E.grad_term(i);
+                const T fev = w * (E.bf + E.rho * e2) + gt, fod = w * T(3) * E.rho * e;
+                const T gev = w * (E.bg + E.phi * e2), god = w * T(3) * E.phi * e;
+                const T kev = w * (E.bk + E.psi * e2), kod = w * T(3) * E.psi * e;
+                sf += T(2) * fev;
+                sg += T(2) * gev;
+                sk += T(2) * kev;
+                Store<S>::st(out, (0 * Q + i) << 5, fi + P.omega[0] * ((fev + fod) - fi), offi);
+                Store<S>::st(out, (0 * Q + o) << 5, fo + P.omega[0] * ((fev - fod) - fo), offi);
+                Store<S>::st(out, (1 * Q + i) << 5, gi + P.omega[1] * ((gev + god) - gi), T(0));
+                Store<S>::st(out, (1 * Q + o) << 5, go + P.omega[1] * ((gev - god) - go), T(0));
+                Store<S>::st(out, (2 * Q + i) << 5, ki + P.omega[2] * ((kev + kod) - ki), T(0));
+                Store<S>::st(out, (2 * Q + o) << 5, ko + P.omega[2] * ((kev - kod) - ko), T(0));
+            }
+            const T off0 = T(rest_offset<Q, S>(0, 0));
+            const T f0 = Store<S>::ld(ctr, 0, off0);
+            const T g0 = Store<S>::ld(ctr, Q << 5, T(0));
+            const T k0 = Store<S>::ld(ctr, (2 * Q) << 5, T(0));
+            Store<S>::st(out, 0, f0 + P.omega[0] * ((E.rho - sf) - f0), off0);
+            Store<S>::st(out, Q << 5, g0 + P.omega[1] * ((E.phi - sg) - g0), T(0));
+            Store<S>::st(out, (2 * Q) << 5, k0 + P.omega[2] * ((E.psi - sk) - k0), T(0));
         }
-        const T off0 = T(rest_offset<Q, S>(0, 0));
-        const T f0 = Store<S>::ld(src, r, off0);
-        const T g0 = Store<S>::ld(src, (long long)Q * g.Np + r, T(0));
-        const T k0 = Store<S>::ld(src, (long long)2 * Q * g.Np + r, T(0));
-        Store<S>::st(dst, r, f0 + P.omega[0] * ((E.rho - sf) - f0), off0);
-        Store<S>::st(dst, (long long)Q * g.Np + r, g0 + P.omega[1] * ((E.phi - sg) - g0), T(0));
-        Store<S>::st(dst, (long long)2 * Q * g.Np + r, k0 + P.omega[2] * ((E.psi - sk) - k0), T(0));
+        jc[0] = jn[0];
+        jc[1] = jn[1];
+        jc[2] = jn[2];
     }
 
     block_sum3(mr, mp, ms);
@@ -231,7 +277,7 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
 
 // ------------------------------------------------------------ host side
 
-// tile variants: 0 = default for the lattice; D3Q19: 1 = 32x8, 2 = 64x4, 3 = 16x16;
+// tile variants: 0 = default (D3Q19 64x4, D2Q9 128); D3Q19: 1 = 32x8, 2 = 64x4, 3 = 16x16;
 // D2Q9: 1 = 128, 2 = 256, 3 = 64.  tile = variant + 16 * chunk (chunk 0 = auto).
 template <int Q>
 struct FusedCfg {
@@ -247,7 +293,7 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
         c.TX = 16;  // double storage: a smaller tile keeps the static shared ring under 48 KB
         c.TY = 8;
     } else if (Q == 19) {
-        const int v = variant == 0 ? 1 : variant;
+        const int v = variant == 0 ? 2 : variant;  // 64x4 measured fastest on 256^3
         c.TX = v == 2 ? 64 : (v == 3 ? 16 : 32);
         c.TY = v == 2 ? 4 : (v == 3 ? 16 : 8);
     } else {
@@ -261,7 +307,7 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
     if (mc <= 0) {
         // enough blocks to fill 152 SMs a few times over, chunks of at most 64 planes
         const long long cols = (long long)((NA + c.TX - 1) / c.TX) * ((NB + c.TY - 1) / c.TY);
-        mc = 64;
+        mc = (Q == 19) ? 16 : 64;
         while (mc > 4 && cols * ((NM + mc - 1) / mc) < 4 * 152) mc >>= 1;
     }
     c.MC = mc < 1 ? 1 : (mc > NM ? NM : mc);
@@ -284,8 +330,7 @@ inline MGeom mgeom(const tlbm_host::DevState& d, const FusedCfg<Q>& c) {
     g.NA = d.nx;
     g.NB = (Q == 19) ? d.ny : 1;
     g.NM = (Q == 19) ? d.nz : d.ny;
-    g.plane = (long long)g.NA * g.NB;
-    g.Np = d.Np;
+    g.rowstride = (long long)d.ncx * 3 * Q * 32;
     g.MC = c.MC;
     g.tilesA = (g.NA + c.TX - 1) / c.TX;
     g.tilesB = (g.NB + c.TY - 1) / c.TY;

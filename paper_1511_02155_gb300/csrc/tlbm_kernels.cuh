@@ -2,10 +2,8 @@
 // (Semprebon, Krueger, Kusumaatmaja, arXiv:1511.02155) and the launch table
 // that the C ABI dispatches through.
 //
-// Device state layout (one A-B pair of population buffers):
-//   pop[b][(s*Q + i)*Np + r], s = set (0 f, 1 g, 2 k), i = direction,
-//   r = x + nx*(y + ny*z); Np = N rounded up to 64 so that each direction
-//   array starts 256-byte aligned.
+// Device state layout: one A-B pair of population buffers in the 32-node chunk
+// layout of tlbm_lattice.cuh (pidx), s = set (0 f, 1 g, 2 k), i = direction.
 // The stored value at (i, r) is the POST-COLLISION population x*_i(r, t-1) of
 // the previous step; the conventional population of the paper is recovered by
 // the pull of Eq. latboltPropagation,
@@ -68,9 +66,11 @@ __device__ __forceinline__ typename Store<S>::T pull(const Geom& g, const S* __r
                              wrap(z - Lat<Q>::cz(i), g.nz));
     if (SOLID && solid[q]) {
         const T off2 = T(rest_offset<Q, S>(s, opp<Q>(i)));
-        return Store<S>::ld(src, (long long)(s * Q + opp<Q>(i)) * g.Np + r, off2);
+        return Store<S>::ld(src, pidx<Q>(g, s, opp<Q>(i), x, y, z), off2);
     }
-    return Store<S>::ld(src, (long long)(s * Q + i) * g.Np + q, off);
+    return Store<S>::ld(src, pidx<Q>(g, s, i, wrap(x - Lat<Q>::cx(i), g.nx), wrap(y - Lat<Q>::cy(i), g.ny),
+                                     wrap(z - Lat<Q>::cz(i), g.nz)),
+                        off);
 }
 
 // ------------------------------------------------- moments (+ mass partials)
@@ -215,17 +215,18 @@ k_collide_split(Geom g, const S* __restrict__ src, S* __restrict__ dst,
     using T = typename Store<S>::T;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
          r += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords(g, r, x, y, z);
+        const long long cb = chunk_base<Q>(g, x, y, z);
         if (SOLID && solid[r]) {
 #pragma unroll
             for (int s = 0; s < 3; ++s)
 #pragma unroll
                 for (int i = 0; i < Q; ++i)
-                    Store<S>::st(dst, (long long)(s * Q + i) * g.Np + r, T(rest_offset<Q, S>(s, i)),
+                    Store<S>::st(dst, cb + ((s * Q + i) << 5), T(rest_offset<Q, S>(s, i)),
                                  T(rest_offset<Q, S>(s, i)));
             continue;
         }
-        int x, y, z;
-        coords(g, r, x, y, z);
         T f[Q], gg[Q], k[Q];
         T rho = T(0), jx = T(0), jy = T(0), jz = T(0), phi = T(0), psi = T(0);
 #pragma unroll
@@ -250,16 +251,16 @@ k_collide_split(Geom g, const S* __restrict__ src, S* __restrict__ dst,
             T fe, ge, ke;
             E.eq(i, fe, ge, ke);
             sf += fe; sg += ge; sk += ke;
-            Store<S>::st(dst, (long long)(0 * Q + i) * g.Np + r, f[i] + P.omega[0] * (fe - f[i]),
+            Store<S>::st(dst, cb + ((0 * Q + i) << 5), f[i] + P.omega[0] * (fe - f[i]),
                          T(rest_offset<Q, S>(0, i)));
-            Store<S>::st(dst, (long long)(1 * Q + i) * g.Np + r, gg[i] + P.omega[1] * (ge - gg[i]),
+            Store<S>::st(dst, cb + ((1 * Q + i) << 5), gg[i] + P.omega[1] * (ge - gg[i]),
                          T(rest_offset<Q, S>(1, i)));
-            Store<S>::st(dst, (long long)(2 * Q + i) * g.Np + r, k[i] + P.omega[2] * (ke - k[i]),
+            Store<S>::st(dst, cb + ((2 * Q + i) << 5), k[i] + P.omega[2] * (ke - k[i]),
                          T(rest_offset<Q, S>(2, i)));
         }
-        Store<S>::st(dst, r, f[0] + P.omega[0] * ((rho - sf) - f[0]), T(rest_offset<Q, S>(0, 0)));
-        Store<S>::st(dst, (long long)Q * g.Np + r, gg[0] + P.omega[1] * ((phi - sg) - gg[0]), T(0));
-        Store<S>::st(dst, (long long)2 * Q * g.Np + r, k[0] + P.omega[2] * ((psi - sk) - k[0]), T(0));
+        Store<S>::st(dst, cb, f[0] + P.omega[0] * ((rho - sf) - f[0]), T(rest_offset<Q, S>(0, 0)));
+        Store<S>::st(dst, cb + (Q << 5), gg[0] + P.omega[1] * ((phi - sg) - gg[0]), T(0));
+        Store<S>::st(dst, cb + ((2 * Q) << 5), k[0] + P.omega[2] * ((psi - sk) - k[0]), T(0));
     }
 }
 
@@ -292,11 +293,12 @@ k_init_eq(Geom g, S* __restrict__ dst, const uint8_t* __restrict__ solid,
         int x, y, z;
         coords(g, r, x, y, z);
         if (SOLID && solid[r]) {
+            const long long cb = chunk_base<Q>(g, x, y, z);
 #pragma unroll
             for (int s = 0; s < 3; ++s)
 #pragma unroll
                 for (int i = 0; i < Q; ++i)
-                    Store<S>::st(dst, (long long)(s * Q + i) * g.Np + r, T(rest_offset<Q, S>(s, i)),
+                    Store<S>::st(dst, cb + ((s * Q + i) << 5), T(rest_offset<Q, S>(s, i)),
                                  T(rest_offset<Q, S>(s, i)));
             continue;
         }
@@ -318,14 +320,14 @@ k_init_eq(Geom g, S* __restrict__ dst, const uint8_t* __restrict__ solid,
         eqv[0][0] = rho - sf; eqv[1][0] = phi - sg; eqv[2][0] = psi - sk;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const long long q = node(g, wrap(x - Lat<Q>::cx(i), g.nx), wrap(y - Lat<Q>::cy(i), g.ny),
-                                     wrap(z - Lat<Q>::cz(i), g.nz));
-            const bool bounce = SOLID && solid[q];
+            const int xs = wrap(x - Lat<Q>::cx(i), g.nx), ys = wrap(y - Lat<Q>::cy(i), g.ny),
+                      zs = wrap(z - Lat<Q>::cz(i), g.nz);
+            const bool bounce = SOLID && solid[node(g, xs, ys, zs)];
             const int j = bounce ? opp<Q>(i) : i;
-            const long long at = bounce ? r : q;
+            const long long at = bounce ? chunk_base<Q>(g, x, y, z) : chunk_base<Q>(g, xs, ys, zs);
 #pragma unroll
             for (int s = 0; s < 3; ++s)
-                Store<S>::st(dst, (long long)(s * Q + j) * g.Np + at, eqv[s][i],
+                Store<S>::st(dst, at + ((s * Q + j) << 5), eqv[s][i],
                              T(bounce ? rest_offset<Q, S>(s, opp<Q>(i)) : rest_offset<Q, S>(s, i)));
         }
     }
@@ -417,7 +419,7 @@ k_set_pops(Geom g, const double* __restrict__ in, const uint8_t* __restrict__ so
                 const T off = T(rest_offset<Q, S>(set, i));
                 double v = bounce ? in[(long long)(set * Q + opp<Q>(i)) * g.N + r]
                                   : in[(long long)(set * Q + i) * g.N + q];
-                Store<S>::st(dst, (long long)(set * Q + i) * g.Np + r, s ? off : T(v), off);
+                Store<S>::st(dst, pidx<Q>(g, set, i, x, y, z), s ? off : T(v), off);
             }
         }
     }

@@ -160,11 +160,36 @@ __host__ __device__ constexpr double rest_offset(int s, int i) {
 
 // ------------------------------------------------------------------ geometry
 
+// Population layout: 32-node chunks along x ("array of structures of arrays").
+// The element of set s, direction i at node (x, y, z) is
+//   ((row * ncx + x/32) * 3Q + s*Q + i) * 32 + x%32,   row = y + ny*z,
+// with ncx = ceil(nx/32).  A warp working on 32 consecutive x of one row finds
+// all 3Q populations of its nodes in one contiguous 3Q*32-element block, so
+// every load or store of a node is one base address plus an immediate offset.
+// Padding nodes (x >= nx in the last chunk) are never read or written.
 struct Geom {
     int nx, ny, nz;
     long long N;   // nodes
-    long long Np;  // stride between direction arrays (N rounded up to 64)
+    long long Np;  // stride of node-indexed moment arrays (N rounded up to 64)
+    int ncx;       // 32-node chunks per row
 };
+
+template <int Q>
+__host__ __device__ __forceinline__ long long chunk_base(const Geom& g, int x, int y, int z) {
+    const long long row = (long long)y + (long long)g.ny * z;
+    return ((row * g.ncx + (x >> 5)) * (3 * Q) << 5) + (x & 31);
+}
+
+template <int Q>
+__host__ __device__ __forceinline__ long long pidx(const Geom& g, int s, int i, int x, int y, int z) {
+    return chunk_base<Q>(g, x, y, z) + ((long long)(s * Q + i) << 5);
+}
+
+// elements of one population buffer
+inline long long pop_elems(int Q, int nx, int ny, int nz) {
+    const long long ncx = (nx + 31) / 32;
+    return (long long)ny * nz * ncx * 32 * 3 * Q;
+}
 
 __device__ __forceinline__ int wrap(int v, int n) {
     v += (v < 0) ? n : 0;

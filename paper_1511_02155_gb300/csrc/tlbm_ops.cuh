@@ -25,7 +25,7 @@ inline Phys<T> to_phys(const PhysD& p) {
     return q;
 }
 
-inline Geom geom(const DevState& d) { return Geom{d.nx, d.ny, d.nz, d.N, d.Np}; }
+inline Geom geom(const DevState& d) { return Geom{d.nx, d.ny, d.nz, d.N, d.Np, d.ncx}; }
 
 inline int grid_for(long long n) {
     long long b = (n + kThreads - 1) / kThreads;
