@@ -58,8 +58,17 @@ __device__ __forceinline__ int xpart(int a) {
     return (a >> 5) * (3 * Q * 32) + (a & 31);
 }
 
-template <int Q, typename S, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+// L2 bulk prefetch (TMA unit) of [p, p + bytes); p 16-byte aligned, bytes a
+// multiple of 16.  A hint: it does not fault and does not wait.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// ILP: a thread's border node loads interleave with its own node's loads.
+// EARLY: phase C's loads are issued before phase M's (values held across M).
+// PF: each warp prefetches its own 32-node chunk three planes ahead into L2.
+template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false>
+__global__ void __launch_bounds__(TX * TY, 2)
 k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename Store<S>::T> P,
         double* __restrict__ partials) {
     using T = typename Store<S>::T;
@@ -135,30 +144,47 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
     auto moments_plane = [&](int m, int slot, T (&j)[3]) {
         const int mm = wrap1(m, g.NM);
         const int zr[3] = {wrap1(mm - 1, g.NM), mm, wrap1(mm + 1, g.NM)};
+        const bool two = nnodes == 2;
+        T rho0 = T(0), ja = T(0), jb = T(0), jm = T(0), phi0 = T(0), psi0 = T(0);
+        T rho1 = T(0), phi1 = T(0), psi1 = T(0);
 #pragma unroll
-        for (int n = 0; n < 2; ++n) {
-            if (n >= nnodes) break;
-            T rho = T(0), ja = T(0), jb = T(0), jm = T(0), phi = T(0), psi = T(0);
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const S* p = src_of(n, zr, A::ca(i), A::cb(i), A::cm(i));
-                const T f = Store<S>::ld(p, (0 * Q + i) << 5, T(rest_offset<Q, S>(0, i)));
-                rho += f;
-                if (A::ca(i)) ja += T(A::ca(i)) * f;
-                if (A::cb(i)) jb += T(A::cb(i)) * f;
-                if (A::cm(i)) jm += T(A::cm(i)) * f;
-                phi += Store<S>::ld(p, (1 * Q + i) << 5, T(0));
-                psi += Store<S>::ld(p, (2 * Q + i) << 5, T(0));
-            }
-            sm[slot][0][h[n]] = rho;
-            sm[slot][1][h[n]] = phi;
-            sm[slot][2][h[n]] = psi;
-            if (n == 0) {
-                j[0] = ja;
-                j[1] = jb;
-                j[2] = jm;
+        for (int i = 0; i < Q; ++i) {
+            const S* p0 = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
+            const T off = T(rest_offset<Q, S>(0, i));
+            const T f = Store<S>::ld(p0, (0 * Q + i) << 5, off);
+            rho0 += f;
+            if (A::ca(i)) ja += T(A::ca(i)) * f;
+            if (A::cb(i)) jb += T(A::cb(i)) * f;
+            if (A::cm(i)) jm += T(A::cm(i)) * f;
+            phi0 += Store<S>::ld(p0, (1 * Q + i) << 5, T(0));
+            psi0 += Store<S>::ld(p0, (2 * Q + i) << 5, T(0));
+            if (ILP && two) {  // border node of this thread, loads interleaved with node 0
+                const S* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
+                rho1 += Store<S>::ld(p1, (0 * Q + i) << 5, off);
+                phi1 += Store<S>::ld(p1, (1 * Q + i) << 5, T(0));
+                psi1 += Store<S>::ld(p1, (2 * Q + i) << 5, T(0));
             }
         }
+        if (!ILP && two) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const S* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
+                rho1 += Store<S>::ld(p1, (0 * Q + i) << 5, T(rest_offset<Q, S>(0, i)));
+                phi1 += Store<S>::ld(p1, (1 * Q + i) << 5, T(0));
+                psi1 += Store<S>::ld(p1, (2 * Q + i) << 5, T(0));
+            }
+        }
+        sm[slot][0][h[0]] = rho0;
+        sm[slot][1][h[0]] = phi0;
+        sm[slot][2][h[0]] = psi0;
+        if (two) {
+            sm[slot][0][h[1]] = rho1;
+            sm[slot][1][h[1]] = phi1;
+            sm[slot][2][h[1]] = psi1;
+        }
+        j[0] = ja;
+        j[1] = jb;
+        j[2] = jm;
     };
 
     double mr = 0.0, mp = 0.0, ms = 0.0;
@@ -168,9 +194,30 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
     moments_plane(M0, M0 & 3, jc);
 
     for (int m = M0; m < M1; ++m) {
+        // Pulled populations of this thread's node at plane m, loaded before the
+        // phase-M loads of plane m+1 so that both sets of requests are in flight
+        // together (these were read one iteration ago and hit in L2).
+        const int zr[3] = {wrap1(m - 1, g.NM), m, wrap1(m + 1, g.NM)};
+        T fv[Q], gv[Q], kv[Q];
+        auto load_node = [&]() {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const S* pi = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
+                fv[i] = Store<S>::ld(pi, (0 * Q + i) << 5, T(rest_offset<Q, S>(0, i)));
+                gv[i] = Store<S>::ld(pi, (1 * Q + i) << 5, T(0));
+                kv[i] = Store<S>::ld(pi, (2 * Q + i) << 5, T(0));
+            }
+        };
+        if (EARLY && active) load_node();
+        if (PF && (tid & 31) == 0 && active && m + 3 <= M1 + 1) {
+            // this warp's chunk of plane m+3: 3Q*32 contiguous populations
+            const long long row = (long long)wrap1(m + 3 >= g.NM ? m + 3 - g.NM : m + 3, g.NM) * g.NB + yb[0][1];
+            prefetch_l2(src + row * g.rowstride + (xp[0][1] & ~31), 3 * Q * 32 * sizeof(S));
+        }
         moments_plane(m + 1, (m + 1) & 3, jn);
         __syncthreads();
         if (active) {
+            if (!EARLY) load_node();
             // ---- derivatives from the ring (pairs of opposite links)
             const int c0 = h[0];
             T X0[3], gA[3], gB[3], gM[3], lp[3];
@@ -218,24 +265,14 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
             ms += (double)X0[2];
 
             // ---- collide + store, direction pairs
-            const int zr[3] = {wrap1(m - 1, g.NM), m, wrap1(m + 1, g.NM)};
             const long long roff = ((long long)m * g.NB + yb[0][1]) * g.rowstride + xp[0][1];
             S* out = dst + roff;
-            const S* ctr = src + roff;
             T sf = T(0), sg = T(0), sk = T(0);
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int o = opp<Q>(i);
                 if (o < i) continue;
-                const S* pi = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
-                const S* po = src_of(0, zr, -A::ca(i), -A::cb(i), -A::cm(i));
                 const T offi = T(rest_offset<Q, S>(0, i));
-                const T fi = Store<S>::ld(pi, (0 * Q + i) << 5, offi);
-                const T fo = Store<S>::ld(po, (0 * Q + o) << 5, offi);
-                const T gi = Store<S>::ld(pi, (1 * Q + i) << 5, T(0));
-                const T go = Store<S>::ld(po, (1 * Q + o) << 5, T(0));
-                const T ki = Store<S>::ld(pi, (2 * Q + i) << 5, T(0));
-                const T ko = Store<S>::ld(po, (2 * Q + o) << 5, T(0));
                 // equilibria of the pair: even part shared, odd part flips sign
                 const T w = T(Lat<Q>::w(i));
                 const T e = E.eu(i);
@@ -247,20 +284,17 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
                 sf += T(2) * fev;
                 sg += T(2) * gev;
                 sk += T(2) * kev;
-                Store<S>::st(out, (0 * Q + i) << 5, fi + P.omega[0] * ((fev + fod) - fi), offi);
-                Store<S>::st(out, (0 * Q + o) << 5, fo + P.omega[0] * ((fev - fod) - fo), offi);
-                Store<S>::st(out, (1 * Q + i) << 5, gi + P.omega[1] * ((gev + god) - gi), T(0));
-                Store<S>::st(out, (1 * Q + o) << 5, go + P.omega[1] * ((gev - god) - go), T(0));
-                Store<S>::st(out, (2 * Q + i) << 5, ki + P.omega[2] * ((kev + kod) - ki), T(0));
-                Store<S>::st(out, (2 * Q + o) << 5, ko + P.omega[2] * ((kev - kod) - ko), T(0));
+                Store<S>::st(out, (0 * Q + i) << 5, fv[i] + P.omega[0] * ((fev + fod) - fv[i]), offi);
+                Store<S>::st(out, (0 * Q + o) << 5, fv[o] + P.omega[0] * ((fev - fod) - fv[o]), offi);
+                Store<S>::st(out, (1 * Q + i) << 5, gv[i] + P.omega[1] * ((gev + god) - gv[i]), T(0));
+                Store<S>::st(out, (1 * Q + o) << 5, gv[o] + P.omega[1] * ((gev - god) - gv[o]), T(0));
+                Store<S>::st(out, (2 * Q + i) << 5, kv[i] + P.omega[2] * ((kev + kod) - kv[i]), T(0));
+                Store<S>::st(out, (2 * Q + o) << 5, kv[o] + P.omega[2] * ((kev - kod) - kv[o]), T(0));
             }
             const T off0 = T(rest_offset<Q, S>(0, 0));
-            const T f0 = Store<S>::ld(ctr, 0, off0);
-            const T g0 = Store<S>::ld(ctr, Q << 5, T(0));
-            const T k0 = Store<S>::ld(ctr, (2 * Q) << 5, T(0));
-            Store<S>::st(out, 0, f0 + P.omega[0] * ((E.rho - sf) - f0), off0);
-            Store<S>::st(out, Q << 5, g0 + P.omega[1] * ((E.phi - sg) - g0), T(0));
-            Store<S>::st(out, (2 * Q) << 5, k0 + P.omega[2] * ((E.psi - sk) - k0), T(0));
+            Store<S>::st(out, 0, fv[0] + P.omega[0] * ((E.rho - sf) - fv[0]), off0);
+            Store<S>::st(out, Q << 5, gv[0] + P.omega[1] * ((E.phi - sg) - gv[0]), T(0));
+            Store<S>::st(out, (2 * Q) << 5, kv[0] + P.omega[2] * ((E.psi - sk) - kv[0]), T(0));
         }
         jc[0] = jn[0];
         jc[1] = jn[1];
@@ -282,15 +316,27 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
 template <int Q>
 struct FusedCfg {
     int TX, TY, MC;
+    int mode;
 };
 
+// d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 64x4,
+// D2Q9 128); D3Q19 1 = 32x8, 2 = 64x4, 3 = 16x16; D2Q9 1 = 128, 2 = 256,
+// 3 = 64.  mode bit 0: interleaved border loads; bit 1: early phase-C loads;
+// bit 2: per-warp L2 prefetch three planes ahead.  mode 0 is the default for
+// the lattice (D3Q19: 1, D2Q9: 4); 6 selects the plain loop.  chunk = planes
+// per block (0 = chosen from the lattice size).
 template <int Q>
 inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
-    const int variant = d.prec == 0 ? 0 : (d.tile & 15);  // double storage: default tile only
-    int mc = d.tile >> 4;
+    const bool dbl = d.prec == 0;  // double storage: one default shape only
+    const int variant = dbl ? 0 : (d.tile & 15);
+    int mc = d.tile >> 8;
     FusedCfg<Q> c{};
-    if (Q == 19 && d.prec == 0) {
-        c.TX = 16;  // double storage: a smaller tile keeps the static shared ring under 48 KB
+    c.mode = dbl ? 0 : ((d.tile >> 4) & 7);
+    // defaults measured on GB300: D3Q19 interleaved border loads (an L2
+    // prefetch thrashes L2 there); D2Q9 per-warp L2 prefetch three planes ahead
+    if (c.mode == 0) c.mode = (Q == 19) ? 1 : 4;
+    if (Q == 19 && dbl) {
+        c.TX = 16;  // double storage: a smaller tile keeps the static shared ring small
         c.TY = 8;
     } else if (Q == 19) {
         const int v = variant == 0 ? 2 : variant;  // 64x4 measured fastest on 256^3
@@ -305,7 +351,7 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
     const int NB = (Q == 19) ? d.ny : 1;
     const int NM = (Q == 19) ? d.nz : d.ny;
     if (mc <= 0) {
-        // enough blocks to fill 152 SMs a few times over, chunks of at most 64 planes
+        // enough blocks to fill 152 SMs a few times over
         const long long cols = (long long)((NA + c.TX - 1) / c.TX) * ((NB + c.TY - 1) / c.TY);
         mc = (Q == 19) ? 16 : 64;
         while (mc > 4 && cols * ((NM + mc - 1) / mc) < 4 * 152) mc >>= 1;
@@ -358,18 +404,40 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
     if (nb > 0x7fffffffLL || nb > d.partials_cap) return cudaErrorInvalidConfiguration;
     const S* src = static_cast<const S*>(d.pop[d.cur]);
     S* dst = static_cast<S*>(d.pop[1 - d.cur]);
+    auto go = [&](auto kern, int threads) { kern<<<(int)nb, threads, 0, st>>>(g, src, dst, P, d.partials); };
     if constexpr (sizeof(S) == 8) {
         // double storage is the parity path: one tile shape per lattice
-        if constexpr (Q == 19) k_fused<Q, S, 16, 8><<<(int)nb, 128, 0, st>>>(g, src, dst, P, d.partials);
-        else k_fused<Q, S, 128, 1><<<(int)nb, 128, 0, st>>>(g, src, dst, P, d.partials);
+        if constexpr (Q == 19) go(k_fused<Q, S, 16, 8, false, false>, 128);
+        else go(k_fused<Q, S, 128, 1, false, false>, 128);
     } else if constexpr (Q == 19) {
-        if (c.TX == 64) k_fused<Q, S, 64, 4><<<(int)nb, 256, 0, st>>>(g, src, dst, P, d.partials);
-        else if (c.TX == 16) k_fused<Q, S, 16, 16><<<(int)nb, 256, 0, st>>>(g, src, dst, P, d.partials);
-        else k_fused<Q, S, 32, 8><<<(int)nb, 256, 0, st>>>(g, src, dst, P, d.partials);
+        if (c.TX == 64) {
+            switch (c.mode) {
+                case 2: go(k_fused<Q, S, 64, 4, false, true>, 256); break;
+                case 4: go(k_fused<Q, S, 64, 4, false, false, true>, 256); break;
+                case 5: go(k_fused<Q, S, 64, 4, true, false, true>, 256); break;
+                case 6: go(k_fused<Q, S, 64, 4, false, false>, 256); break;
+                default: go(k_fused<Q, S, 64, 4, true, false>, 256);
+            }
+        } else if (c.TX == 16) {
+            go(k_fused<Q, S, 16, 16, false, false>, 256);
+        } else {
+            go(k_fused<Q, S, 32, 8, false, false>, 256);
+        }
     } else {
-        if (c.TX == 256) k_fused<Q, S, 256, 1><<<(int)nb, 256, 0, st>>>(g, src, dst, P, d.partials);
-        else if (c.TX == 64) k_fused<Q, S, 64, 1><<<(int)nb, 64, 0, st>>>(g, src, dst, P, d.partials);
-        else k_fused<Q, S, 128, 1><<<(int)nb, 128, 0, st>>>(g, src, dst, P, d.partials);
+        if (c.TX == 256) {
+            switch (c.mode) {
+                case 1: go(k_fused<Q, S, 256, 1, true, false>, 256); break;
+                case 2: go(k_fused<Q, S, 256, 1, false, true>, 256); break;
+                case 3: go(k_fused<Q, S, 256, 1, true, true>, 256); break;
+                default: go(k_fused<Q, S, 256, 1, false, false>, 256);
+            }
+        } else if (c.TX == 64) {
+            go(k_fused<Q, S, 64, 1, false, false>, 64);
+        } else if (c.mode == 4) {
+            go(k_fused<Q, S, 128, 1, false, false, true>, 128);
+        } else {
+            go(k_fused<Q, S, 128, 1, false, false>, 128);  // plain loop
+        }
     }
     return cudaGetLastError();
 }

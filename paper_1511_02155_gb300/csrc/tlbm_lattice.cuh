@@ -111,8 +111,8 @@ __host__ __device__ constexpr double tens(int i, int c) {
 // ------------------------------------------------------------------ storage
 
 // Population storage formats.  Plain float/double store the value; the 16-bit
-// formats store the offset from the rest state (w_i for f at rho_0 = 1, zero
-// for g and k) and compute in float.
+// formats store the offset from the rest state (w_i for f at rho_0 = 1,
+// zero for g and k) and compute in float.
 template <typename S>
 struct Store;
 
