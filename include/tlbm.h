@@ -205,6 +205,45 @@ tlbm_status tlbm_set_state(tlbm *t, const void *host, size_t bytes);
 /* Kernel launches per tlbm_step(1) of the current configuration. */
 int tlbm_launches_per_step(const tlbm *t);
 
+/*
+ * One time step on caller-owned device buffers, allocating nothing.
+ * The paper has no counterpart: this is an engineering entry point for callers
+ * that may not allocate device memory themselves -- code embedded in a host
+ * framework that owns every device allocation through its own pool, loops that
+ * must not pay allocation latency, and code running where cudaMalloc is not
+ * allowed (while a stream is being captured into a CUDA graph).
+ *   lattice, nx, ny, nz, kappa, alpha, tau_f, M_phi, M_psi, h: as tlbm_create
+ *                 (Gamma_phi = Gamma_psi = 1).
+ *   precision     TLBM_FP32 or TLBM_FP64 only.
+ *   solid_dev     device array of nx*ny*nz bytes (nonzero = solid) or NULL.
+ *   src_dev       device populations in the engine's raw state layout (the bytes
+ *                 tlbm_get_state returns, tlbm_state_bytes long); read only.
+ *   dst_dev       device buffer of the same size; receives the state one step
+ *                 later.  Must not overlap src_dev.
+ *   mass_dev      device array of 3 doubles for the FP64 totals of the input
+ *                 state (sum rho, phi, psi over fluid nodes), or NULL.
+ *   cuda_stream   stream to run on (NULL = default stream).
+ * The step is the split implementation (moments, ghosts, collide + stream).
+ * Its intermediate arrays live in one fixed 8 MiB __device__ buffer per device,
+ * which limits the lattice to 349504 nodes in FP64 and 699008 nodes in FP32;
+ * larger lattices return TLBM_ERR_ARG before any device work.  Every GPU that
+ * loads the library holds that buffer until the process exits.  All calls share
+ * it and it keeps the last call's contents, so calls whose kernels overlap on
+ * the GPU (other streams, other host threads) race: serialise them.  The first
+ * call on a device looks up the buffer's device address (cudaGetSymbolAddress);
+ * make that first call outside any stream capture.  Returns without waiting.
+ * Errors: TLBM_ERR_ARG / TLBM_ERR_PARAM / TLBM_ERR_UNSUPPORTED on the host
+ * checks, TLBM_ERR_CUDA if a launch fails; tlbm_noalloc_last_error() has the
+ * message.
+ */
+tlbm_status tlbm_step_noalloc(tlbm_lattice lattice, tlbm_precision precision, int nx, int ny, int nz,
+                              const double kappa[3], double alpha, double tau_f, double M_phi,
+                              double M_psi, const double h[3], const uint8_t *solid_dev,
+                              const void *src_dev, void *dst_dev, double *mass_dev, void *cuda_stream);
+
+/* Message of the last failed tlbm_step_noalloc call on this host thread ("" if none). */
+const char *tlbm_noalloc_last_error(void);
+
 /* Message of the last failed call on this handle ("" if none; never NULL). */
 const char *tlbm_last_error(const tlbm *t);
 

@@ -26,6 +26,7 @@ UNITS = {
     "tlbm_f32.cu": [],
     "tlbm_f16.cu": [],
     "tlbm_bf16.cu": [],
+    "tlbm_noalloc.cu": ["-fmad=false"],
 }
 
 
