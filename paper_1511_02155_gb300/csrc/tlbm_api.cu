@@ -204,7 +204,11 @@ tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz
     d.nx = nx; d.ny = ny; d.nz = nz; d.N = N;
     d.Np = (N + 63) / 64 * 64;
     d.ncx = (nx + 31) / 32;
-    d.pop_elems = (long long)ny * nz * d.ncx * 32 * 3 * d.Q;
+    // bytes of one 32-node chunk (see the layout notes in tlbm_lattice.cuh): all
+    // 3Q populations of the storage type, or for the 16-bit formats 3(Q-1)
+    // 16-bit moving populations plus three FP32 rest populations
+    const long long chunk = esize == 2 ? (3LL * (d.Q - 1) * 32 * 2 + 3LL * 32 * 4) : 3LL * d.Q * 32 * (long long)esize;
+    d.pop_bytes = (long long)ny * nz * d.ncx * chunk;
     d.cur = 0;
     d.tile = 0;
     set_phys(t);
@@ -214,7 +218,7 @@ tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz
         tlbm_destroy(t);
         return s;
     };
-    const size_t popbytes = esize * (size_t)d.pop_elems;
+    const size_t popbytes = (size_t)d.pop_bytes;
     for (int b = 0; b < 2; ++b) {
         cudaError_t e = cudaMalloc(&d.pop[b], popbytes);
         if (e != cudaSuccess)
@@ -446,7 +450,7 @@ tlbm_status tlbm_set_populations(tlbm* t, const double* host) {
 
 size_t tlbm_state_bytes(const tlbm* t) {
     if (!t) return 0;
-    return t->esize * (size_t)t->d.pop_elems;
+    return (size_t)t->d.pop_bytes;
 }
 
 tlbm_status tlbm_get_state(tlbm* t, void* host, size_t bytes) {

@@ -42,7 +42,7 @@ struct MGeom {
     int NA, NB, NM;       // extents along a, b, m
     int MC;               // planes per chunk
     int tilesA, tilesB;   // tiles per plane
-    long long rowstride;  // elements between consecutive (b, m) rows: ncx * 3Q * 32
+    long long rowstride;  // bytes between consecutive (b, m) rows: ncx * chunk bytes
 };
 
 __device__ __forceinline__ int modp(int v, int n) {
@@ -53,10 +53,6 @@ __device__ __forceinline__ int modp(int v, int n) {
 // single periodic wrap of v in [-n, 2n)
 __device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
-template <int Q>
-__device__ __forceinline__ int xpart(int a) {
-    return (a >> 5) * (3 * Q * 32) + (a & 31);
-}
 
 // L2 bulk prefetch (TMA unit) of [p, p + bytes); p 16-byte aligned, bytes a
 // multiple of 16.  A hint: it does not fault and does not wait.
@@ -99,7 +95,7 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
     // Node 0 of every thread: its own tile slot (coordinates wrap for threads past
     // the lattice edge, whose slots serve as the periodic halo of active ones).
     // Node 1: one border slot of the halo ring, for tid < NBORDER.
-    int h[2], xp[2][3], yb[2][3];
+    int h[2], xc[2][3], yb[2][3];  // ring slot; byte offsets of x-1, x, x+1 in a row; rows b-1, b, b+1
     {
         int hx[2], hy[2];
         hx[0] = tx + 1;
@@ -123,9 +119,9 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
             h[n] = hy[n] * HW + hx[n];
             const int aa = modp(A0 + hx[n] - 1, g.NA);
             const int bb = (D == 3) ? modp(B0 + hy[n] - HY, g.NB) : 0;
-            xp[n][0] = xpart<Q>(wrap1(aa - 1, g.NA));
-            xp[n][1] = xpart<Q>(aa);
-            xp[n][2] = xpart<Q>(wrap1(aa + 1, g.NA));
+            const int xs[3] = {wrap1(aa - 1, g.NA), aa, wrap1(aa + 1, g.NA)};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) xc[n][k] = (xs[k] >> 5) * (int)Fmt<Q, S>::CHUNK + (xs[k] & 31) * Fmt<Q, S>::ESZ;
             yb[n][0] = (D == 3) ? wrap1(bb - 1, g.NB) : 0;
             yb[n][1] = bb;
             yb[n][2] = (D == 3) ? wrap1(bb + 1, g.NB) : 0;
@@ -133,15 +129,17 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
     }
     const int nnodes = tid < NBORDER ? 2 : 1;
 
-    // base pointer of the pull source of direction i for node n at plane rows zr
-    auto src_of = [&](int n, const int (&zr)[3], int ca, int cb, int cm) -> const S* {
+    const unsigned char* srcb = reinterpret_cast<const unsigned char*>(src);
+    // pull source of direction (ca, cb, cm) for node n at plane rows zr
+    auto src_of = [&](int n, const int (&zr)[3], int ca, int cb, int cm) -> const unsigned char* {
         const long long row = (long long)zr[1 - cm] * g.NB + yb[n][1 - cb];
-        return src + row * g.rowstride + xp[n][1 - ca];
+        return srcb + row * g.rowstride + xc[n][1 - ca];
     };
 
     // Phase M: moments of plane m for this thread's nodes into ring slot `slot`;
-    // node 0's momentum density is returned in j.
-    auto moments_plane = [&](int m, int slot, T (&j)[3]) {
+    // node 0's momentum density is returned in j and its summed f deviations
+    // (rho - 1 in the 16-bit formats, rho otherwise) in rd.
+    auto moments_plane = [&](int m, int slot, T (&j)[3], T& rd) {
         const int mm = wrap1(m, g.NM);
         const int zr[3] = {wrap1(mm - 1, g.NM), mm, wrap1(mm + 1, g.NM)};
         const bool two = nnodes == 2;
@@ -149,30 +147,34 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
         T rho1 = T(0), phi1 = T(0), psi1 = T(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const S* p0 = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
-            const T off = T(rest_offset<Q, S>(0, i));
-            const T f = Store<S>::ld(p0, (0 * Q + i) << 5, off);
+            const unsigned char* p0 = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
+            const T f = Fmt<Q, S>::ld_delta(p0, 0, i);
             rho0 += f;
             if (A::ca(i)) ja += T(A::ca(i)) * f;
             if (A::cb(i)) jb += T(A::cb(i)) * f;
             if (A::cm(i)) jm += T(A::cm(i)) * f;
-            phi0 += Store<S>::ld(p0, (1 * Q + i) << 5, T(0));
-            psi0 += Store<S>::ld(p0, (2 * Q + i) << 5, T(0));
+            phi0 += Fmt<Q, S>::ld_delta(p0, 1, i);
+            psi0 += Fmt<Q, S>::ld_delta(p0, 2, i);
             if (ILP && two) {  // border node of this thread, loads interleaved with node 0
-                const S* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                rho1 += Store<S>::ld(p1, (0 * Q + i) << 5, off);
-                phi1 += Store<S>::ld(p1, (1 * Q + i) << 5, T(0));
-                psi1 += Store<S>::ld(p1, (2 * Q + i) << 5, T(0));
+                const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
+                rho1 += Fmt<Q, S>::ld_delta(p1, 0, i);
+                phi1 += Fmt<Q, S>::ld_delta(p1, 1, i);
+                psi1 += Fmt<Q, S>::ld_delta(p1, 2, i);
             }
         }
         if (!ILP && two) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const S* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                rho1 += Store<S>::ld(p1, (0 * Q + i) << 5, T(rest_offset<Q, S>(0, i)));
-                phi1 += Store<S>::ld(p1, (1 * Q + i) << 5, T(0));
-                psi1 += Store<S>::ld(p1, (2 * Q + i) << 5, T(0));
+                const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
+                rho1 += Fmt<Q, S>::ld_delta(p1, 0, i);
+                phi1 += Fmt<Q, S>::ld_delta(p1, 1, i);
+                psi1 += Fmt<Q, S>::ld_delta(p1, 2, i);
             }
+        }
+        rd = rho0;
+        if (Fmt<Q, S>::PACKED) {  // sums of f deviations: rho - 1
+            rho0 += T(1);
+            rho1 += T(1);
         }
         sm[slot][0][h[0]] = rho0;
         sm[slot][1][h[0]] = phi0;
@@ -188,10 +190,10 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
     };
 
     double mr = 0.0, mp = 0.0, ms = 0.0;
-    T jc[3], jn[3];
+    T jc[3], jn[3], rdc, rdn;
 
-    moments_plane(M0 - 1, (M0 + 3) & 3, jn);
-    moments_plane(M0, M0 & 3, jc);
+    moments_plane(M0 - 1, (M0 + 3) & 3, jn, rdn);
+    moments_plane(M0, M0 & 3, jc, rdc);
 
     for (int m = M0; m < M1; ++m) {
         // Pulled populations of this thread's node at plane m, loaded before the
@@ -202,19 +204,20 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
         auto load_node = [&]() {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const S* pi = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
-                fv[i] = Store<S>::ld(pi, (0 * Q + i) << 5, T(rest_offset<Q, S>(0, i)));
-                gv[i] = Store<S>::ld(pi, (1 * Q + i) << 5, T(0));
-                kv[i] = Store<S>::ld(pi, (2 * Q + i) << 5, T(0));
+                const unsigned char* pi = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
+                fv[i] = Fmt<Q, S>::ld(pi, 0, i);
+                gv[i] = Fmt<Q, S>::ld(pi, 1, i);
+                kv[i] = Fmt<Q, S>::ld(pi, 2, i);
             }
         };
         if (EARLY && active) load_node();
         if (PF && (tid & 31) == 0 && active && m + 3 <= M1 + 1) {
-            // this warp's chunk of plane m+3: 3Q*32 contiguous populations
+            // this warp's chunk of plane m+3 (all populations of its 32 nodes)
             const long long row = (long long)wrap1(m + 3 >= g.NM ? m + 3 - g.NM : m + 3, g.NM) * g.NB + yb[0][1];
-            prefetch_l2(src + row * g.rowstride + (xp[0][1] & ~31), 3 * Q * 32 * sizeof(S));
+            prefetch_l2(srcb + row * g.rowstride + xc[0][1] - ((A0 + tx) & 31) * Fmt<Q, S>::ESZ,
+                        (unsigned)Fmt<Q, S>::CHUNK);
         }
-        moments_plane(m + 1, (m + 1) & 3, jn);
+        moments_plane(m + 1, (m + 1) & 3, jn, rdn);
         __syncthreads();
         if (active) {
             if (!EARLY) load_node();
@@ -260,19 +263,20 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
             NodeEq<Q, T> E;
             if (D == 3) E.setup(P, X0[0], jc[0], jc[1], jc[2], X0[1], X0[2], grad, lap);
             else E.setup(P, X0[0], jc[0], jc[2], T(0), X0[1], X0[2], grad, lap);
-            mr += (double)X0[0];
+            mr += rho_total<Q, S>(rdc);
             mp += (double)X0[1];
             ms += (double)X0[2];
 
             // ---- collide + store, direction pairs
-            const long long roff = ((long long)m * g.NB + yb[0][1]) * g.rowstride + xp[0][1];
-            S* out = dst + roff;
-            T sf = T(0), sg = T(0), sk = T(0);
+            unsigned char* out = reinterpret_cast<unsigned char*>(dst) +
+                                 ((long long)m * g.NB + yb[0][1]) * g.rowstride + xc[0][1];
+
+            T sf = T(0), sg = T(0), sk = T(0);  // sums of the moving equilibria
+            T qf = T(0), qg = T(0), qk = T(0);  // sums of the moving populations as stored
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int o = opp<Q>(i);
                 if (o < i) continue;
-                const T offi = T(rest_offset<Q, S>(0, i));
                 // equilibria of the pair: even part shared, odd part flips sign
                 const T w = T(Lat<Q>::w(i));
                 const T e = E.eu(i);
@@ -284,21 +288,37 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
                 sf += T(2) * fev;
                 sg += T(2) * gev;
                 sk += T(2) * kev;
-                Store<S>::st(out, (0 * Q + i) << 5, fv[i] + P.omega[0] * ((fev + fod) - fv[i]), offi);
-                Store<S>::st(out, (0 * Q + o) << 5, fv[o] + P.omega[0] * ((fev - fod) - fv[o]), offi);
-                Store<S>::st(out, (1 * Q + i) << 5, gv[i] + P.omega[1] * ((gev + god) - gv[i]), T(0));
-                Store<S>::st(out, (1 * Q + o) << 5, gv[o] + P.omega[1] * ((gev - god) - gv[o]), T(0));
-                Store<S>::st(out, (2 * Q + i) << 5, kv[i] + P.omega[2] * ((kev + kod) - kv[i]), T(0));
-                Store<S>::st(out, (2 * Q + o) << 5, kv[o] + P.omega[2] * ((kev - kod) - kv[o]), T(0));
+                const T v[6] = {fv[i] + P.omega[0] * ((fev + fod) - fv[i]), fv[o] + P.omega[0] * ((fev - fod) - fv[o]),
+                                gv[i] + P.omega[1] * ((gev + god) - gv[i]), gv[o] + P.omega[1] * ((gev - god) - gv[o]),
+                                kv[i] + P.omega[2] * ((kev + kod) - kv[i]), kv[o] + P.omega[2] * ((kev - kod) - kv[o])};
+                Fmt<Q, S>::st(out, 0, i, v[0]);
+                Fmt<Q, S>::st(out, 0, o, v[1]);
+                Fmt<Q, S>::st(out, 1, i, v[2]);
+                Fmt<Q, S>::st(out, 1, o, v[3]);
+                Fmt<Q, S>::st(out, 2, i, v[4]);
+                Fmt<Q, S>::st(out, 2, o, v[5]);
+                if (Fmt<Q, S>::PACKED) {
+                    qf += Fmt<Q, S>::qdelta(0, i, v[0]) + Fmt<Q, S>::qdelta(0, o, v[1]);
+                    qg += Fmt<Q, S>::qdelta(1, i, v[2]) + Fmt<Q, S>::qdelta(1, o, v[3]);
+                    qk += Fmt<Q, S>::qdelta(2, i, v[4]) + Fmt<Q, S>::qdelta(2, o, v[5]);
+                }
             }
-            const T off0 = T(rest_offset<Q, S>(0, 0));
-            Store<S>::st(out, 0, fv[0] + P.omega[0] * ((E.rho - sf) - fv[0]), off0);
-            Store<S>::st(out, Q << 5, gv[0] + P.omega[1] * ((E.phi - sg) - gv[0]), T(0));
-            Store<S>::st(out, (2 * Q) << 5, kv[0] + P.omega[2] * ((E.psi - sk) - kv[0]), T(0));
+            if (Fmt<Q, S>::PACKED) {
+                // rest = moment - stored moving populations (deviations for f):
+                // conserves rho, phi, psi through the 16-bit rounding
+                Fmt<Q, S>::st_delta(out, 0, 0, rdc - qf);
+                Fmt<Q, S>::st_delta(out, 1, 0, E.phi - qg);
+                Fmt<Q, S>::st_delta(out, 2, 0, E.psi - qk);
+            } else {
+                Fmt<Q, S>::st(out, 0, 0, fv[0] + P.omega[0] * ((E.rho - sf) - fv[0]));
+                Fmt<Q, S>::st(out, 1, 0, gv[0] + P.omega[1] * ((E.phi - sg) - gv[0]));
+                Fmt<Q, S>::st(out, 2, 0, kv[0] + P.omega[2] * ((E.psi - sk) - kv[0]));
+            }
         }
         jc[0] = jn[0];
         jc[1] = jn[1];
         jc[2] = jn[2];
+        rdc = rdn;
     }
 
     block_sum3(mr, mp, ms);
@@ -370,36 +390,36 @@ inline int fused_launches(const tlbm_host::DevState&) {
     return 1;
 }
 
-template <int Q>
+template <int Q, typename S>
 inline MGeom mgeom(const tlbm_host::DevState& d, const FusedCfg<Q>& c) {
     MGeom g;
     g.NA = d.nx;
     g.NB = (Q == 19) ? d.ny : 1;
     g.NM = (Q == 19) ? d.nz : d.ny;
-    g.rowstride = (long long)d.ncx * 3 * Q * 32;
+    g.rowstride = (long long)d.ncx * Fmt<Q, S>::CHUNK;
     g.MC = c.MC;
     g.tilesA = (g.NA + c.TX - 1) / c.TX;
     g.tilesB = (g.NB + c.TY - 1) / c.TY;
     return g;
 }
 
-template <int Q>
+template <int Q, typename S>
 inline long long fused_blocks(const tlbm_host::DevState& d) {
     const FusedCfg<Q> c = fused_cfg<Q>(d);
-    const MGeom g = mgeom<Q>(d, c);
+    const MGeom g = mgeom<Q, S>(d, c);
     return (long long)g.tilesA * g.tilesB * ((g.NM + g.MC - 1) / g.MC);
 }
 
 // number of partial sums the last step wrote (for k_mass_final)
 template <int Q, typename S>
 inline int fused_partials(const tlbm_host::DevState& d, int kind) {
-    return kind == tlbm_host::KIND_FUSED ? (int)fused_blocks<Q>(d) : kMassBlocks;
+    return kind == tlbm_host::KIND_FUSED ? (int)fused_blocks<Q, S>(d) : kMassBlocks;
 }
 
 template <int Q, typename S>
 inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<S>::T>& P, cudaStream_t st) {
     const FusedCfg<Q> c = fused_cfg<Q>(d);
-    const MGeom g = mgeom<Q>(d, c);
+    const MGeom g = mgeom<Q, S>(d, c);
     const long long nb = (long long)g.tilesA * g.tilesB * ((g.NM + g.MC - 1) / g.MC);
     if (nb > 0x7fffffffLL || nb > d.partials_cap) return cudaErrorInvalidConfiguration;
     const S* src = static_cast<const S*>(d.pop[d.cur]);

@@ -25,7 +25,7 @@ struct DevState {
     int nx, ny, nz;
     long long N, Np;     // nodes; stride of node-indexed moment arrays
     int ncx;             // 32-node chunks per row of the population layout
-    long long pop_elems; // elements of one population buffer
+    long long pop_bytes; // bytes of one population buffer
     void* pop[2];        // A-B population buffers (chunk layout, see tlbm_lattice.cuh)
     int cur;             // buffer holding the current state
     const uint8_t* solid;  // device mask (nullptr when there are no solid nodes)

@@ -3,7 +3,7 @@
 // that the C ABI dispatches through.
 //
 // Device state layout: one A-B pair of population buffers in the 32-node chunk
-// layout of tlbm_lattice.cuh (pidx), s = set (0 f, 1 g, 2 k), i = direction.
+// layout of tlbm_lattice.cuh (Fmt), s = set (0 f, 1 g, 2 k), i = direction.
 // The stored value at (i, r) is the POST-COLLISION population x*_i(r, t-1) of
 // the previous step; the conventional population of the paper is recovered by
 // the pull of Eq. latboltPropagation,
@@ -60,17 +60,30 @@ template <int Q, typename S, bool SOLID>
 __device__ __forceinline__ typename Store<S>::T pull(const Geom& g, const S* __restrict__ src,
                                                       const uint8_t* __restrict__ solid, int s,
                                                       int i, int x, int y, int z, long long r) {
-    using T = typename Store<S>::T;
-    const T off = T(rest_offset<Q, S>(s, i));
-    const long long q = node(g, wrap(x - Lat<Q>::cx(i), g.nx), wrap(y - Lat<Q>::cy(i), g.ny),
-                             wrap(z - Lat<Q>::cz(i), g.nz));
-    if (SOLID && solid[q]) {
-        const T off2 = T(rest_offset<Q, S>(s, opp<Q>(i)));
-        return Store<S>::ld(src, pidx<Q>(g, s, opp<Q>(i), x, y, z), off2);
-    }
-    return Store<S>::ld(src, pidx<Q>(g, s, i, wrap(x - Lat<Q>::cx(i), g.nx), wrap(y - Lat<Q>::cy(i), g.ny),
-                                     wrap(z - Lat<Q>::cz(i), g.nz)),
-                        off);
+    const int xs = wrap(x - Lat<Q>::cx(i), g.nx), ys = wrap(y - Lat<Q>::cy(i), g.ny),
+              zs = wrap(z - Lat<Q>::cz(i), g.nz);
+    if (SOLID && solid[node(g, xs, ys, zs)]) return pld<Q, S>(src, g, s, opp<Q>(i), x, y, z);
+    return pld<Q, S>(src, g, s, i, xs, ys, zs);
+}
+
+// The same population as stored: its deviation from Fmt::bias (f_i - w_i in the
+// 16-bit formats, the value itself otherwise).
+template <int Q, typename S, bool SOLID>
+__device__ __forceinline__ typename Store<S>::T pull_delta(const Geom& g, const S* __restrict__ src,
+                                                            const uint8_t* __restrict__ solid, int s,
+                                                            int i, int x, int y, int z) {
+    const int xs = wrap(x - Lat<Q>::cx(i), g.nx), ys = wrap(y - Lat<Q>::cy(i), g.ny),
+              zs = wrap(z - Lat<Q>::cz(i), g.nz);
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(src);
+    if (SOLID && solid[node(g, xs, ys, zs)]) return Fmt<Q, S>::ld_delta(b + node_off<Q, S>(g, x, y, z), s, opp<Q>(i));
+    return Fmt<Q, S>::ld_delta(b + node_off<Q, S>(g, xs, ys, zs), s, i);
+}
+
+// rho of a node from the sum rd of its stored f deviations (16-bit formats keep
+// f - w, whose sum is rho - 1)
+template <int Q, typename S>
+__device__ __forceinline__ double rho_total(typename Store<S>::T rd) {
+    return Fmt<Q, S>::PACKED ? 1.0 + (double)rd : (double)rd;
 }
 
 // ------------------------------------------------- moments (+ mass partials)
@@ -88,16 +101,17 @@ k_moments(Geom g, const S* __restrict__ src, const uint8_t* __restrict__ solid,
          r += (long long)gridDim.x * blockDim.x) {
         int x, y, z;
         coords(g, r, x, y, z);
-        T rho = T(0), phi = T(0), psi = T(0);
+        T rd = T(0), phi = T(0), psi = T(0);
         if (!(SOLID && solid[r])) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                rho += pull<Q, S, SOLID>(g, src, solid, 0, i, x, y, z, r);
-                phi += pull<Q, S, SOLID>(g, src, solid, 1, i, x, y, z, r);
-                psi += pull<Q, S, SOLID>(g, src, solid, 2, i, x, y, z, r);
+                rd += pull_delta<Q, S, SOLID>(g, src, solid, 0, i, x, y, z);
+                phi += pull_delta<Q, S, SOLID>(g, src, solid, 1, i, x, y, z);
+                psi += pull_delta<Q, S, SOLID>(g, src, solid, 2, i, x, y, z);
             }
-            sr += (double)rho; sp += (double)phi; ss += (double)psi;
+            sr += rho_total<Q, S>(rd); sp += (double)phi; ss += (double)psi;
         }
+        const T rho = (SOLID && solid[r]) ? T(0) : T(rho_total<Q, S>(rd));
         if (WRITE) {
             mom[r] = rho;
             mom[g.Np + r] = phi;
@@ -217,50 +231,64 @@ k_collide_split(Geom g, const S* __restrict__ src, S* __restrict__ dst,
          r += (long long)gridDim.x * blockDim.x) {
         int x, y, z;
         coords(g, r, x, y, z);
-        const long long cb = chunk_base<Q>(g, x, y, z);
+        unsigned char* cb = reinterpret_cast<unsigned char*>(dst) + node_off<Q, S>(g, x, y, z);
         if (SOLID && solid[r]) {
 #pragma unroll
             for (int s = 0; s < 3; ++s)
 #pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    Store<S>::st(dst, cb + ((s * Q + i) << 5), T(rest_offset<Q, S>(s, i)),
-                                 T(rest_offset<Q, S>(s, i)));
+                for (int i = 0; i < Q; ++i) Fmt<Q, S>::st(cb, s, i, T(Fmt<Q, S>::bias(s, i)));
             continue;
         }
         T f[Q], gg[Q], k[Q];
-        T rho = T(0), jx = T(0), jy = T(0), jz = T(0), phi = T(0), psi = T(0);
+        T rd = T(0), jx = T(0), jy = T(0), jz = T(0), phi = T(0), psi = T(0);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            f[i] = pull<Q, S, SOLID>(g, src, solid, 0, i, x, y, z, r);
-            gg[i] = pull<Q, S, SOLID>(g, src, solid, 1, i, x, y, z, r);
-            k[i] = pull<Q, S, SOLID>(g, src, solid, 2, i, x, y, z, r);
-            rho += f[i];
-            if (Lat<Q>::cx(i)) jx += T(Lat<Q>::cx(i)) * f[i];
-            if (Lat<Q>::cy(i)) jy += T(Lat<Q>::cy(i)) * f[i];
-            if (Lat<Q>::cz(i)) jz += T(Lat<Q>::cz(i)) * f[i];
+            const T fd = pull_delta<Q, S, SOLID>(g, src, solid, 0, i, x, y, z);
+            f[i] = fd + T(Fmt<Q, S>::bias(0, i));
+            gg[i] = pull_delta<Q, S, SOLID>(g, src, solid, 1, i, x, y, z);
+            k[i] = pull_delta<Q, S, SOLID>(g, src, solid, 2, i, x, y, z);
+            rd += fd;
+            if (Lat<Q>::cx(i)) jx += T(Lat<Q>::cx(i)) * fd;
+            if (Lat<Q>::cy(i)) jy += T(Lat<Q>::cy(i)) * fd;
+            if (Lat<Q>::cz(i)) jz += T(Lat<Q>::cz(i)) * fd;
             phi += gg[i];
             psi += k[i];
         }
+        const T rho = Fmt<Q, S>::PACKED ? T(1) + rd : rd;
         T grad[3][3], lap[3];
         derivs<Q, T>(g, mom, x, y, z, r, grad, lap);
         NodeEq<Q, T> E;
         E.setup(P, rho, jx, jy, jz, phi, psi, grad, lap);
-        T sf = T(0), sg = T(0), sk = T(0);
+        T sf = T(0), sg = T(0), sk = T(0);  // sums of the moving equilibria
+        T qf = T(0), qg = T(0), qk = T(0);  // sums of the moving populations as stored
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             T fe, ge, ke;
             E.eq(i, fe, ge, ke);
             sf += fe; sg += ge; sk += ke;
-            Store<S>::st(dst, cb + ((0 * Q + i) << 5), f[i] + P.omega[0] * (fe - f[i]),
-                         T(rest_offset<Q, S>(0, i)));
-            Store<S>::st(dst, cb + ((1 * Q + i) << 5), gg[i] + P.omega[1] * (ge - gg[i]),
-                         T(rest_offset<Q, S>(1, i)));
-            Store<S>::st(dst, cb + ((2 * Q + i) << 5), k[i] + P.omega[2] * (ke - k[i]),
-                         T(rest_offset<Q, S>(2, i)));
+            const T vf = f[i] + P.omega[0] * (fe - f[i]);
+            const T vg = gg[i] + P.omega[1] * (ge - gg[i]);
+            const T vk = k[i] + P.omega[2] * (ke - k[i]);
+            Fmt<Q, S>::st(cb, 0, i, vf);
+            Fmt<Q, S>::st(cb, 1, i, vg);
+            Fmt<Q, S>::st(cb, 2, i, vk);
+            if (Fmt<Q, S>::PACKED) {
+                qf += Fmt<Q, S>::qdelta(0, i, vf);
+                qg += Fmt<Q, S>::qdelta(1, i, vg);
+                qk += Fmt<Q, S>::qdelta(2, i, vk);
+            }
         }
-        Store<S>::st(dst, cb, f[0] + P.omega[0] * ((rho - sf) - f[0]), T(rest_offset<Q, S>(0, 0)));
-        Store<S>::st(dst, cb + (Q << 5), gg[0] + P.omega[1] * ((phi - sg) - gg[0]), T(0));
-        Store<S>::st(dst, cb + ((2 * Q) << 5), k[0] + P.omega[2] * ((psi - sk) - k[0]), T(0));
+        if (Fmt<Q, S>::PACKED) {
+            // rest = moment - stored moving populations (deviations for f):
+            // conserves rho, phi, psi through the 16-bit rounding
+            Fmt<Q, S>::st_delta(cb, 0, 0, rd - qf);
+            Fmt<Q, S>::st_delta(cb, 1, 0, phi - qg);
+            Fmt<Q, S>::st_delta(cb, 2, 0, psi - qk);
+        } else {
+            Fmt<Q, S>::st(cb, 0, 0, f[0] + P.omega[0] * ((rho - sf) - f[0]));
+            Fmt<Q, S>::st(cb, 1, 0, gg[0] + P.omega[1] * ((phi - sg) - gg[0]));
+            Fmt<Q, S>::st(cb, 2, 0, k[0] + P.omega[2] * ((psi - sk) - k[0]));
+        }
     }
 }
 
@@ -293,13 +321,10 @@ k_init_eq(Geom g, S* __restrict__ dst, const uint8_t* __restrict__ solid,
         int x, y, z;
         coords(g, r, x, y, z);
         if (SOLID && solid[r]) {
-            const long long cb = chunk_base<Q>(g, x, y, z);
 #pragma unroll
             for (int s = 0; s < 3; ++s)
 #pragma unroll
-                for (int i = 0; i < Q; ++i)
-                    Store<S>::st(dst, cb + ((s * Q + i) << 5), T(rest_offset<Q, S>(s, i)),
-                                 T(rest_offset<Q, S>(s, i)));
+                for (int i = 0; i < Q; ++i) pst<Q, S>(dst, g, s, i, x, y, z, T(Fmt<Q, S>::bias(s, i)));
             continue;
         }
         const T rho = mom[r], phi = mom[g.Np + r], psi = mom[2 * g.Np + r];
@@ -323,12 +348,11 @@ k_init_eq(Geom g, S* __restrict__ dst, const uint8_t* __restrict__ solid,
             const int xs = wrap(x - Lat<Q>::cx(i), g.nx), ys = wrap(y - Lat<Q>::cy(i), g.ny),
                       zs = wrap(z - Lat<Q>::cz(i), g.nz);
             const bool bounce = SOLID && solid[node(g, xs, ys, zs)];
-            const int j = bounce ? opp<Q>(i) : i;
-            const long long at = bounce ? chunk_base<Q>(g, x, y, z) : chunk_base<Q>(g, xs, ys, zs);
 #pragma unroll
-            for (int s = 0; s < 3; ++s)
-                Store<S>::st(dst, at + ((s * Q + j) << 5), eqv[s][i],
-                             T(bounce ? rest_offset<Q, S>(s, opp<Q>(i)) : rest_offset<Q, S>(s, i)));
+            for (int s = 0; s < 3; ++s) {
+                if (bounce) pst<Q, S>(dst, g, s, opp<Q>(i), x, y, z, eqv[s][i]);
+                else pst<Q, S>(dst, g, s, i, xs, ys, zs, eqv[s][i]);
+            }
         }
     }
 }
@@ -346,21 +370,21 @@ k_fields(Geom g, const S* __restrict__ src, const uint8_t* __restrict__ solid, d
          r += (long long)gridDim.x * blockDim.x) {
         int x, y, z;
         coords(g, r, x, y, z);
-        T rho = T(0), jx = T(0), jy = T(0), jz = T(0), phi = T(0), psi = T(0);
+        T rd = T(0), jx = T(0), jy = T(0), jz = T(0), phi = T(0), psi = T(0);
         const bool s = SOLID && solid[r];
         if (!s) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const T f = pull<Q, S, SOLID>(g, src, solid, 0, i, x, y, z, r);
-                rho += f;
-                if (Lat<Q>::cx(i)) jx += T(Lat<Q>::cx(i)) * f;
-                if (Lat<Q>::cy(i)) jy += T(Lat<Q>::cy(i)) * f;
-                if (Lat<Q>::cz(i)) jz += T(Lat<Q>::cz(i)) * f;
-                phi += pull<Q, S, SOLID>(g, src, solid, 1, i, x, y, z, r);
-                psi += pull<Q, S, SOLID>(g, src, solid, 2, i, x, y, z, r);
+                const T fd = pull_delta<Q, S, SOLID>(g, src, solid, 0, i, x, y, z);
+                rd += fd;
+                if (Lat<Q>::cx(i)) jx += T(Lat<Q>::cx(i)) * fd;
+                if (Lat<Q>::cy(i)) jy += T(Lat<Q>::cy(i)) * fd;
+                if (Lat<Q>::cz(i)) jz += T(Lat<Q>::cz(i)) * fd;
+                phi += pull_delta<Q, S, SOLID>(g, src, solid, 1, i, x, y, z);
+                psi += pull_delta<Q, S, SOLID>(g, src, solid, 2, i, x, y, z);
             }
         }
-        const double dr = (double)rho, dp = (double)phi, ds = (double)psi;
+        const double dr = s ? 0.0 : rho_total<Q, S>(rd), dp = (double)phi, ds = (double)psi;
         if (C1) C1[r] = s ? 0.0 : 0.5 * (dr + dp - ds);
         if (C2) C2[r] = s ? 0.0 : 0.5 * (dr - dp - ds);
         if (C3) C3[r] = s ? 0.0 : ds;
@@ -416,10 +440,9 @@ k_set_pops(Geom g, const double* __restrict__ in, const uint8_t* __restrict__ so
             const bool bounce = SOLID && solid[q];
 #pragma unroll
             for (int set = 0; set < 3; ++set) {
-                const T off = T(rest_offset<Q, S>(set, i));
-                double v = bounce ? in[(long long)(set * Q + opp<Q>(i)) * g.N + r]
-                                  : in[(long long)(set * Q + i) * g.N + q];
-                Store<S>::st(dst, pidx<Q>(g, set, i, x, y, z), s ? off : T(v), off);
+                const double v = bounce ? in[(long long)(set * Q + opp<Q>(i)) * g.N + r]
+                                        : in[(long long)(set * Q + i) * g.N + q];
+                pst<Q, S>(dst, g, set, i, x, y, z, s ? T(Fmt<Q, S>::bias(set, i)) : T(v));
             }
         }
     }

@@ -110,63 +110,59 @@ __host__ __device__ constexpr double tens(int i, int c) {
 
 // ------------------------------------------------------------------ storage
 
-// Population storage formats.  Plain float/double store the value; the 16-bit
-// formats store the offset from the rest state (w_i for f at rho_0 = 1,
-// zero for g and k) and compute in float.
+// Scalar conversions of the storage types (compute type T).
 template <typename S>
 struct Store;
 
 template <>
 struct Store<double> {
     using T = double;
-    static __device__ __forceinline__ double ld(const double* p, long long o, double) { return p[o]; }
-    static __device__ __forceinline__ void st(double* p, long long o, double v, double) { p[o] = v; }
+    static __device__ __forceinline__ double get(double v) { return v; }
+    static __device__ __forceinline__ double put(double v) { return v; }
 };
 
 template <>
 struct Store<float> {
     using T = float;
-    static __device__ __forceinline__ float ld(const float* p, long long o, float) { return p[o]; }
-    static __device__ __forceinline__ void st(float* p, long long o, float v, float) { p[o] = v; }
+    static __device__ __forceinline__ float get(float v) { return v; }
+    static __device__ __forceinline__ float put(float v) { return v; }
 };
 
 template <>
 struct Store<__half> {
     using T = float;
-    static __device__ __forceinline__ float ld(const __half* p, long long o, float off) {
-        return __half2float(p[o]) + off;
-    }
-    static __device__ __forceinline__ void st(__half* p, long long o, float v, float off) {
-        p[o] = __float2half_rn(v - off);
-    }
+    static __device__ __forceinline__ float get(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half put(float v) { return __float2half_rn(v); }
 };
 
 template <>
 struct Store<__nv_bfloat16> {
     using T = float;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16* p, long long o, float off) {
-        return __bfloat162float(p[o]) + off;
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16* p, long long o, float v, float off) {
-        p[o] = __float2bfloat16_rn(v - off);
-    }
+    static __device__ __forceinline__ float get(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 put(float v) { return __float2bfloat16_rn(v); }
 };
-
-// rest-state offset of direction i of set s (only used by the offset formats)
-template <int Q, typename S>
-__host__ __device__ constexpr double rest_offset(int s, int i) {
-    return (sizeof(S) == 2 && s == 0) ? Lat<Q>::w(i) : 0.0;
-}
 
 // ------------------------------------------------------------------ geometry
 
-// Population layout: 32-node chunks along x ("array of structures of arrays").
-// The element of set s, direction i at node (x, y, z) is
-//   ((row * ncx + x/32) * 3Q + s*Q + i) * 32 + x%32,   row = y + ny*z,
-// with ncx = ceil(nx/32).  A warp working on 32 consecutive x of one row finds
-// all 3Q populations of its nodes in one contiguous 3Q*32-element block, so
-// every load or store of a node is one base address plus an immediate offset.
-// Padding nodes (x >= nx in the last chunk) are never read or written.
+// Population layout: 32-node chunks along x.  All populations of the 32 nodes
+// x = 32c .. 32c+31 of one row (row = y + ny*z) form one contiguous chunk of
+// Fmt<Q,S>::CHUNK bytes at ((row * ncx + c) * CHUNK), ncx = ceil(nx / 32).
+// Inside a chunk, each run holds one value per lane (node), sizeof(S) bytes
+// apart, so a node is one byte offset: chunk + lane * sizeof(S).
+//   FP64 / FP32: 3Q runs of S, run s*Q + i for set s, direction i.
+//   16-bit formats (packed): f is kept as its deviation f_i - w_i from the
+//     rest state at rho = 1, g and k as they are.  The 3(Q-1) moving directions
+//     i >= 1 are 16-bit runs; the rest populations f_0 - w_0, g_0, k_0 are FP32,
+//     each split into a run of low and a run of high 16-bit halves.  The rest
+//     populations carry nearly all of phi and psi, which 16 bits would round by
+//     up to 2.4e-4 per step; the moving populations are small.  A collision
+//     writes each rest population as the node's moment minus the moving
+//     populations as stored (rounded), so the 16-bit rounding moves mass
+//     between directions of a node but never changes it; rho - 1 is summed from
+//     the small deviations, which keeps FP32 rounding from biasing the totals.
+// A warp on 32 consecutive x of one row therefore finds all populations of its
+// nodes in one chunk: each load or store is one base address plus an immediate
+// offset.  Padding nodes (x >= nx in the last chunk) are never read or written.
 struct Geom {
     int nx, ny, nz;
     long long N;   // nodes
@@ -174,21 +170,81 @@ struct Geom {
     int ncx;       // 32-node chunks per row
 };
 
-template <int Q>
-__host__ __device__ __forceinline__ long long chunk_base(const Geom& g, int x, int y, int z) {
+template <int Q, typename S>
+struct Fmt {
+    using T = typename Store<S>::T;
+    static constexpr bool PACKED = sizeof(S) == 2;
+    static constexpr int ESZ = (int)sizeof(S);  // bytes between lanes of a run
+    static constexpr long long CHUNK = PACKED ? (3LL * Q + 3) * 32 * 2 : 3LL * Q * 32 * ESZ;
+    // byte offset of lane 0 of the run of (s, i) (packed rest: its low halves)
+    __host__ __device__ static constexpr int off(int s, int i) {
+        return PACKED ? (i == 0 ? (3 * (Q - 1) + 2 * s) * 32 * 2 : (s * (Q - 1) + i - 1) * 32 * 2)
+                      : (s * Q + i) * 32 * ESZ;
+    }
+    // rest-state value subtracted before storage (packed formats, set f)
+    __host__ __device__ static constexpr double bias(int s, int i) {
+        return (PACKED && s == 0) ? Lat<Q>::w(i) : 0.0;
+    }
+    // stored value of (s, i) at node pointer n (chunk + lane * ESZ): x - bias
+    static __device__ __forceinline__ T ld_delta(const unsigned char* n, int s, int i) {
+        if constexpr (PACKED) {
+            if (i == 0) {
+                const unsigned lo = *reinterpret_cast<const unsigned short*>(n + off(s, 0));
+                const unsigned hi = *reinterpret_cast<const unsigned short*>(n + off(s, 0) + 64);
+                return __uint_as_float(lo | (hi << 16));
+            }
+            return Store<S>::get(*reinterpret_cast<const S*>(n + off(s, i)));
+        } else {
+            return *reinterpret_cast<const S*>(n + off(s, i));
+        }
+    }
+    // population (s, i) at node pointer n
+    static __device__ __forceinline__ T ld(const unsigned char* n, int s, int i) {
+        return ld_delta(n, s, i) + T(bias(s, i));
+    }
+    // store the deviation d = x - bias of (s, i)
+    static __device__ __forceinline__ void st_delta(unsigned char* n, int s, int i, T d) {
+        if constexpr (PACKED) {
+            if (i == 0) {
+                const unsigned u = __float_as_uint(d);
+                *reinterpret_cast<unsigned short*>(n + off(s, 0)) = (unsigned short)(u & 0xffffu);
+                *reinterpret_cast<unsigned short*>(n + off(s, 0) + 64) = (unsigned short)(u >> 16);
+            } else {
+                *reinterpret_cast<S*>(n + off(s, i)) = Store<S>::put(d);
+            }
+        } else {
+            *reinterpret_cast<S*>(n + off(s, i)) = d;
+        }
+    }
+    static __device__ __forceinline__ void st(unsigned char* n, int s, int i, T v) {
+        st_delta(n, s, i, v - T(bias(s, i)));
+    }
+    // the deviation a store of population value v leaves in memory, as read back
+    static __device__ __forceinline__ T qdelta(int s, int i, T v) {
+        if constexpr (PACKED) {
+            if (i > 0) return Store<S>::get(Store<S>::put(v - T(bias(s, i))));
+        }
+        return v - T(bias(s, i));
+    }
+};
+
+// byte offset of node (x, y, z) in a population buffer: its chunk plus its lane
+template <int Q, typename S>
+__host__ __device__ __forceinline__ long long node_off(const Geom& g, int x, int y, int z) {
     const long long row = (long long)y + (long long)g.ny * z;
-    return ((row * g.ncx + (x >> 5)) * (3 * Q) << 5) + (x & 31);
+    return (row * g.ncx + (x >> 5)) * Fmt<Q, S>::CHUNK + (x & 31) * Fmt<Q, S>::ESZ;
 }
 
-template <int Q>
-__host__ __device__ __forceinline__ long long pidx(const Geom& g, int s, int i, int x, int y, int z) {
-    return chunk_base<Q>(g, x, y, z) + ((long long)(s * Q + i) << 5);
+template <int Q, typename S>
+__device__ __forceinline__ typename Store<S>::T pld(const void* base, const Geom& g, int s, int i, int x,
+                                                    int y, int z) {
+    return Fmt<Q, S>::ld(static_cast<const unsigned char*>(base) + node_off<Q, S>(g, x, y, z), s, i);
 }
 
-// elements of one population buffer
-inline long long pop_elems(int Q, int nx, int ny, int nz) {
-    const long long ncx = (nx + 31) / 32;
-    return (long long)ny * nz * ncx * 32 * 3 * Q;
+template <int Q, typename S>
+__device__ __forceinline__ void pst(void* base, const Geom& g, int s, int i, int x, int y, int z,
+                                    typename Store<S>::T v) {
+    Fmt<Q, S>::st(static_cast<unsigned char*>(base) + node_off<Q, S>(g, x, y, z), s, i, v);
 }
 
 __device__ __forceinline__ int wrap(int v, int n) {
