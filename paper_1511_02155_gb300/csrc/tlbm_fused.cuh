@@ -271,26 +271,33 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
             unsigned char* out = reinterpret_cast<unsigned char*>(dst) +
                                  ((long long)m * g.NB + yb[0][1]) * g.rowstride + xc[0][1];
 
-            T sf = T(0), sg = T(0), sk = T(0);  // sums of the moving equilibria
+            // BGK with omega folded into the equilibria: x* = (1 - omega) x + omega x_eq,
+            // and omega x_eq = EV +- OD for a pair of opposite links, where
+            // EV = w (B + R (e.u)^2) [+ gradient terms for f] and OD = w O (e.u)
+            const T cf = T(1) - P.omega[0], cg = T(1) - P.omega[1], ck = T(1) - P.omega[2];
+            const T Bf = P.omega[0] * E.bf, Rf = T(4.5) * P.omega[0] * E.rho, Of = T(3) * P.omega[0] * E.rho;
+            const T Bg = P.omega[1] * E.bg, Rg = T(4.5) * P.omega[1] * E.phi, Og = T(3) * P.omega[1] * E.phi;
+            const T Bk = P.omega[2] * E.bk, Rk = T(4.5) * P.omega[2] * E.psi, Ok = T(3) * P.omega[2] * E.psi;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) E.Gs[c] *= P.omega[0];
+            T sf = T(0), sg = T(0), sk = T(0);  // sums of omega x_eq over moving links
             T qf = T(0), qg = T(0), qk = T(0);  // sums of the moving populations as stored
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
                 const int o = opp<Q>(i);
                 if (o < i) continue;
-                // equilibria of the pair: even part shared, odd part flips sign
                 const T w = T(Lat<Q>::w(i));
                 const T e = E.eu(i);
-                const T e2 = T(4.5) * e * e;
-                const T gt = E.grad_term(i);
-                const T fev = w * (E.bf + E.rho * e2) + gt, fod = w * T(3) * E.rho * e;
-                const T gev = w * (E.bg + E.phi * e2), god = w * T(3) * E.phi * e;
-                const T kev = w * (E.bk + E.psi * e2), kod = w * T(3) * E.psi * e;
-                sf += T(2) * fev;
-                sg += T(2) * gev;
-                sk += T(2) * kev;
-                const T v[6] = {fv[i] + P.omega[0] * ((fev + fod) - fv[i]), fv[o] + P.omega[0] * ((fev - fod) - fv[o]),
-                                gv[i] + P.omega[1] * ((gev + god) - gv[i]), gv[o] + P.omega[1] * ((gev - god) - gv[o]),
-                                kv[i] + P.omega[2] * ((kev + kod) - kv[i]), kv[o] + P.omega[2] * ((kev - kod) - kv[o])};
+                const T e2 = e * e;
+                const T evf = w * (Bf + Rf * e2) + E.grad_term(i), odf = (w * Of) * e;
+                const T evg = w * (Bg + Rg * e2), odg = (w * Og) * e;
+                const T evk = w * (Bk + Rk * e2), odk = (w * Ok) * e;
+                sf += T(2) * evf;
+                sg += T(2) * evg;
+                sk += T(2) * evk;
+                const T v[6] = {cf * fv[i] + (evf + odf), cf * fv[o] + (evf - odf),
+                                cg * gv[i] + (evg + odg), cg * gv[o] + (evg - odg),
+                                ck * kv[i] + (evk + odk), ck * kv[o] + (evk - odk)};
                 Fmt<Q, S>::st(out, 0, i, v[0]);
                 Fmt<Q, S>::st(out, 0, o, v[1]);
                 Fmt<Q, S>::st(out, 1, i, v[2]);
@@ -310,9 +317,10 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
                 Fmt<Q, S>::st_delta(out, 1, 0, E.phi - qg);
                 Fmt<Q, S>::st_delta(out, 2, 0, E.psi - qk);
             } else {
-                Fmt<Q, S>::st(out, 0, 0, fv[0] + P.omega[0] * ((E.rho - sf) - fv[0]));
-                Fmt<Q, S>::st(out, 1, 0, gv[0] + P.omega[1] * ((E.phi - sg) - gv[0]));
-                Fmt<Q, S>::st(out, 2, 0, kv[0] + P.omega[2] * ((E.psi - sk) - kv[0]));
+                // omega x_eq_0 = omega X - sum of omega x_eq over the moving links
+                Fmt<Q, S>::st(out, 0, 0, cf * fv[0] + (P.omega[0] * E.rho - sf));
+                Fmt<Q, S>::st(out, 1, 0, cg * gv[0] + (P.omega[1] * E.phi - sg));
+                Fmt<Q, S>::st(out, 2, 0, ck * kv[0] + (P.omega[2] * E.psi - sk));
             }
         }
         jc[0] = jn[0];
