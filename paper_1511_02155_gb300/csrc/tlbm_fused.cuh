@@ -64,7 +64,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // EARLY: phase C's loads are issued before phase M's (values held across M).
 // PF: each warp prefetches its own 32-node chunk three planes ahead into L2.
 template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false>
-__global__ void __launch_bounds__(TX * TY, 2)
+__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))  // 16 warps per SM
 k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename Store<S>::T> P,
         double* __restrict__ partials) {
     using T = typename Store<S>::T;
@@ -339,7 +339,7 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
 
 // ------------------------------------------------------------ host side
 
-// tile variants: 0 = default (D3Q19 64x4, D2Q9 128); D3Q19: 1 = 32x8, 2 = 64x4, 3 = 16x16;
+// tile variants: 0 = default (D3Q19 32x4, D2Q9 128); D3Q19: 1 = 32x8, 2 = 64x4, 3 = 32x4;
 // D2Q9: 1 = 128, 2 = 256, 3 = 64.  tile = variant + 16 * chunk (chunk 0 = auto).
 template <int Q>
 struct FusedCfg {
@@ -347,11 +347,12 @@ struct FusedCfg {
     int mode;
 };
 
-// d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 64x4,
-// D2Q9 128); D3Q19 1 = 32x8, 2 = 64x4, 3 = 16x16; D2Q9 1 = 128, 2 = 256,
+// d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 32x4,
+// D2Q9 128); D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4; D2Q9 1 = 128, 2 = 256,
 // 3 = 64.  mode bit 0: interleaved border loads; bit 1: early phase-C loads;
 // bit 2: per-warp L2 prefetch three planes ahead.  mode 0 is the default for
-// the lattice (D3Q19: 1, D2Q9: 4); 6 selects the plain loop.  chunk = planes
+// the shape and format (D3Q19 32x4: plain for FP32, 4 for 16-bit storage;
+// other D3Q19: 1; D2Q9: 4); 6 selects the plain loop.  chunk = planes
 // per block (0 = chosen from the lattice size).
 template <int Q>
 inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
@@ -359,22 +360,25 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
     const int variant = dbl ? 0 : (d.tile & 15);
     int mc = d.tile >> 8;
     FusedCfg<Q> c{};
-    c.mode = dbl ? 0 : ((d.tile >> 4) & 7);
-    // defaults measured on GB300: D3Q19 interleaved border loads (an L2
-    // prefetch thrashes L2 there); D2Q9 per-warp L2 prefetch three planes ahead
-    if (c.mode == 0) c.mode = (Q == 19) ? 1 : 4;
     if (Q == 19 && dbl) {
         c.TX = 16;  // double storage: a smaller tile keeps the static shared ring small
         c.TY = 8;
     } else if (Q == 19) {
-        const int v = variant == 0 ? 2 : variant;  // 64x4 measured fastest on 256^3
-        c.TX = v == 2 ? 64 : (v == 3 ? 16 : 32);
-        c.TY = v == 2 ? 4 : (v == 3 ? 16 : 8);
+        const int v = variant == 0 ? 3 : variant;  // 32x4 measured fastest on 256^3
+        c.TX = v == 2 ? 64 : 32;
+        c.TY = v == 2 ? 4 : (v == 3 ? 4 : 8);
     } else {
         const int v = variant == 0 ? 1 : variant;
         c.TX = v == 2 ? 256 : (v == 3 ? 64 : 128);
         c.TY = 1;
     }
+    c.mode = dbl ? 0 : ((d.tile >> 4) & 7);
+    // defaults measured on GB300: D3Q19 32x4 plain loop for 4-byte storage and
+    // per-warp L2 prefetch for the 16-bit formats (a plane of FP32 populations
+    // is too large for the prefetch to stay in L2); 64x4 and 32x8 interleaved
+    // border loads; D2Q9 per-warp L2 prefetch three planes ahead
+    if (c.mode == 0)
+        c.mode = (Q == 19) ? (c.TX == 32 && c.TY == 4 ? (d.prec >= 2 ? 4 : 6) : 1) : 4;
     const int NA = d.nx;
     const int NB = (Q == 19) ? d.ny : 1;
     const int NM = (Q == 19) ? d.nz : d.ny;
@@ -446,10 +450,15 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
                 case 6: go(k_fused<Q, S, 64, 4, false, false>, 256); break;
                 default: go(k_fused<Q, S, 64, 4, true, false>, 256);
             }
-        } else if (c.TX == 16) {
-            go(k_fused<Q, S, 16, 16, false, false>, 256);
+        } else if (c.TY == 4) {
+            switch (c.mode) {
+                case 1: go(k_fused<Q, S, 32, 4, true, false>, 128); break;
+                case 4: go(k_fused<Q, S, 32, 4, false, false, true>, 128); break;
+                default: go(k_fused<Q, S, 32, 4, false, false>, 128);
+            }
         } else {
-            go(k_fused<Q, S, 32, 8, false, false>, 256);
+            if (c.mode == 6) go(k_fused<Q, S, 32, 8, false, false>, 256);
+            else go(k_fused<Q, S, 32, 8, true, false>, 256);
         }
     } else {
         if (c.TX == 256) {
