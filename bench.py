@@ -35,7 +35,15 @@ sys.path.insert(0, ROOT)
 from paper_1511_02155_gb300 import workloads as W  # noqa: E402
 
 METRIC = "MLUPS and % HBM roofline per ternary step (FP32 vs FP16-store) at fixed error"
-STORE_BYTES = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def bytes_per_node(Q: int, precision: str) -> int:
+    """Algorithmic bytes of one node update: every stored population read once and
+    written once.  FP64/FP32 store 3Q values; the 16-bit formats store the 3(Q-1)
+    moving populations in 2 bytes and the three rest populations in 4."""
+    if precision in ("fp16", "bf16"):
+        return 2 * (3 * (Q - 1) * 2 + 3 * 4)
+    return 2 * 3 * Q * {"fp64": 8, "fp32": 4}[precision]
 
 
 def workload(name: str, size: int = 0):
@@ -61,9 +69,11 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_from_profiles(kernel_tag: str, source_digest: str):
-    """DRAM bytes per launch from a committed ncu summary, or None if the summary
-    is missing or was taken on a different kernel source."""
+def traffic_from_profiles(kernel_tag: str, source_digest: str, nodes: int):
+    """DRAM bytes (read + write) of one launch of this configuration, from the
+    committed ncu summary profiles/traffic.json, scaled by node count from the
+    captured case; None if there is no capture of this configuration or it was
+    taken on a different kernel source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -72,7 +82,7 @@ def traffic_from_profiles(kernel_tag: str, source_digest: str):
     e = d.get(kernel_tag)
     if not e or e.get("source_sha256") != source_digest:
         return None
-    return float(e["dram_bytes_per_launch"])
+    return round(float(e["dram_bytes_per_node"]) * nodes)
 
 
 def kernel_source_digest():
@@ -312,13 +322,13 @@ def main():
     kms, ksteps = eng.kernel_time()
     eng.set_timing(False)
     kernel_ms = kms / max(ksteps, 1)
-    s = STORE_BYTES[args.precision]
-    alg_bytes = 2 * 3 * Q * s * N  # every population read once and written once
+    bpn = bytes_per_node(Q, args.precision)
+    alg_bytes = bpn * N  # every population read once and written once
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     kind = eng.kernel
     tag = f"{kind}:{args.workload}:{args.precision}:{args.tile}"
-    traffic = traffic_from_profiles(tag, kernel_source_digest())
+    traffic = traffic_from_profiles(tag, kernel_source_digest(), N)
 
     # end to end through the public API with host buffers: upload the fields from
     # pinned memory, K steps, download C_1..3 and the mass totals
@@ -355,7 +365,7 @@ def main():
                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
                          "kernel_ms": round(kernel_ms, 4),
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "bytes_per_node": 2 * 3 * Q * s},
+                         "bytes_per_node": bpn},
             "e2e": e2e,
             "gpu_launches": args.steps * eng.launches_per_step,
             "clocks": clocks,
