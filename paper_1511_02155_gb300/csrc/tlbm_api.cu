@@ -134,6 +134,7 @@ void tlbm_destroy(tlbm* t) {
     cudaFree(t->d.pop[0]);
     cudaFree(t->d.pop[1]);
     cudaFree((void*)t->d.solid);
+    cudaFree(t->d.nbm);
     cudaFree(t->d.mom);
     cudaFree(t->d.partials);
     cudaFree(t->d.step_mass);
@@ -237,6 +238,10 @@ tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz
         d.solid = ds;
         e = cudaMemcpy(ds, solid_mask, (size_t)N, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return bail(fail(t, TLBM_ERR_CUDA, "cudaMemcpy(mask): %s", cudaGetErrorString(e)));
+        // neighbour-solid bits of the fused step, built by its first launch
+        e = cudaMalloc(&d.nbm, sizeof(uint32_t) * (size_t)N);
+        if (e != cudaSuccess) return bail(fail(t, TLBM_ERR_OOM, "cudaMalloc(neighbour mask): %s", cudaGetErrorString(e)));
+        d.nbm_ready = 0;
     }
     // mass partials: step partials (up to one per fused block) + tlbm_mass partials
     long long nblk = 0;
@@ -275,7 +280,7 @@ tlbm_status tlbm_set_kernel(tlbm* t, tlbm_kernel kind) {
     if (kind != TLBM_KERNEL_AUTO && kind != TLBM_KERNEL_FUSED && kind != TLBM_KERNEL_SPLIT)
         return fail(t, TLBM_ERR_ARG, "unknown kernel kind");
     if (kind == TLBM_KERNEL_FUSED && !t->ops->has_fused(t->d))
-        return fail(t, TLBM_ERR_UNSUPPORTED, "fused step not built for this configuration (solid nodes)");
+        return fail(t, TLBM_ERR_UNSUPPORTED, "fused step not available for this configuration");
     t->kind_req = kind;
     return TLBM_OK;
 }

@@ -337,6 +337,325 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
     }
 }
 
+// ------------------------------------------------------ solid-aware variant
+
+// Bit i (1 <= i < Q) of nbm[r]: the pull source r - e_i of node r is solid;
+// bit 0: r itself is solid.  Built once per lattice.
+template <int Q>
+__global__ void k_nbmask(Geom g, const uint8_t* __restrict__ solid, uint32_t* __restrict__ nbm) {
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
+         r += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords(g, r, x, y, z);
+        uint32_t m = solid[r] ? 1u : 0u;
+#pragma unroll
+        for (int i = 1; i < Q; ++i)
+            if (solid[node(g, wrap(x - Lat<Q>::cx(i), g.nx), wrap(y - Lat<Q>::cy(i), g.ny),
+                           wrap(z - Lat<Q>::cz(i), g.nz))])
+                m |= 1u << i;
+        nbm[r] = m;
+    }
+}
+
+// One step with solid nodes, halfway bounce-back and wetting ghosts.  As
+// k_fused, but the ghost value of a solid node needs the moments of its fluid
+// neighbours, so each block keeps a two-node halo and works two planes ahead:
+//   M(m+2): moments of plane m+2 over tile + 2-node halo (solid nodes: 0)
+//   barrier
+//   G(m+1): ghost values of the solid nodes of plane m+1 over tile + 1-node halo
+//           (mean over fluid axis neighbours of X - G_X; with only diagonal
+//           fluid neighbours, of X - sqrt(2) G_X)
+//   barrier
+//   C(m):   derivatives, equilibria, BGK and store for the fluid tile nodes.
+// The moment and mask rings have five plane slots and the momentum ring four, so
+// a fast warp writing plane m+2 never touches data a slow warp still reads.
+template <int Q, typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
+k_fused_solid(MGeom g, const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ nbm,
+              Phys<typename Store<S>::T> P, double* __restrict__ partials) {
+    using T = typename Store<S>::T;
+    using A = Axes<Q>;
+    constexpr int D = Lat<Q>::D;
+    constexpr int H = 2;                  // halo width along a
+    constexpr int HB = (D == 3) ? 2 : 0;  // halo width along b
+    constexpr int HW = TX + 2 * H;
+    constexpr int HH = TY + 2 * HB;
+    constexpr int HN = HW * HH;
+    constexpr int NT = TX * TY;
+    constexpr int KS = (HN + NT - 1) / NT;  // region nodes per thread
+    constexpr int R = 5;                    // plane slots of the rings
+    static_assert(D == 3 || TY == 1, "2-D tiles are one row");
+    static_assert(KS <= 3, "at most three region nodes per thread");
+
+    __shared__ T sm[R][3][HN];       // effective rho, phi, psi (ghosts on solid nodes)
+    __shared__ uint32_t sk[R][HN];   // neighbour masks
+    __shared__ T sj[4][4][NT];       // j and summed f deviations of the tile
+
+    const int tid = threadIdx.x;
+    const int tx = tid % TX, ty = tid / TX;
+    const int tileA = blockIdx.x % g.tilesA;
+    const int rest = blockIdx.x / g.tilesA;
+    const int tileB = rest % g.tilesB;
+    const int chunk = rest / g.tilesB;
+    const int A0 = tileA * TX, B0 = tileB * TY;
+    const int M0 = chunk * g.MC;
+    const int M1 = min(M0 + g.MC, g.NM);
+    const bool active = (A0 + tx < g.NA) && (B0 + ty < g.NB);
+    const long long plane = (long long)g.NA * g.NB;
+
+    // this thread's region nodes h = tid + k NT: in-plane node index, pull-source
+    // byte offsets along a and rows along b
+    int xc[KS][3], yb[KS][3], rin[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+        const int h = min(tid + k * NT, HN - 1);
+        const int hx = h % HW, hy = h / HW;
+        const int aa = modp(A0 + hx - H, g.NA);
+        const int bb = (D == 3) ? modp(B0 + hy - HB, g.NB) : 0;
+        const int xs[3] = {wrap1(aa - 1, g.NA), aa, wrap1(aa + 1, g.NA)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xc[k][c] = (xs[c] >> 5) * (int)Fmt<Q, S>::CHUNK + (xs[c] & 31) * Fmt<Q, S>::ESZ;
+        yb[k][0] = (D == 3) ? wrap1(bb - 1, g.NB) : 0;
+        yb[k][1] = bb;
+        yb[k][2] = (D == 3) ? wrap1(bb + 1, g.NB) : 0;
+        rin[k] = aa + g.NA * bb;
+    }
+    // the thread's own tile node (phase C): byte offsets of a-1, a, a+1, rows b-1, b, b+1
+    int xo[3], yo[3];
+    {
+        const int aa = modp(A0 + tx, g.NA), bb = (D == 3) ? modp(B0 + ty, g.NB) : 0;
+        const int xs[3] = {wrap1(aa - 1, g.NA), aa, wrap1(aa + 1, g.NA)};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xo[c] = (xs[c] >> 5) * (int)Fmt<Q, S>::CHUNK + (xs[c] & 31) * Fmt<Q, S>::ESZ;
+        yo[0] = (D == 3) ? wrap1(bb - 1, g.NB) : 0;
+        yo[1] = bb;
+        yo[2] = (D == 3) ? wrap1(bb + 1, g.NB) : 0;
+    }
+    const unsigned char* srcb = reinterpret_cast<const unsigned char*>(src);
+    auto row_ptr = [&](int k, const int (&zr)[3], int cb, int cm) -> const unsigned char* {
+        return srcb + ((long long)zr[1 - cm] * g.NB + yb[k][1 - cb]) * g.rowstride;
+    };
+    auto own_row = [&](const int (&zr)[3], int cb, int cm) -> const unsigned char* {
+        return srcb + ((long long)zr[1 - cm] * g.NB + yo[1 - cb]) * g.rowstride;
+    };
+
+    // M: moments of plane m (node k's pulled populations, bounce-back at solids)
+    auto moments_plane = [&](int m) {
+        const int mm = modp(m, g.NM), slot = modp(m, R), js = modp(m, 4);
+        const int zr[3] = {wrap1(mm - 1, g.NM), mm, wrap1(mm + 1, g.NM)};
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int h = tid + k * NT;
+            if (h >= HN) break;
+            const uint32_t mk = nbm[(long long)mm * plane + rin[k]];
+            T rd = T(0), ja = T(0), jb = T(0), jm = T(0), phi = T(0), psi = T(0);
+            if (!(mk & 1u)) {
+                const unsigned char* own = row_ptr(k, zr, 0, 0) + xc[k][1];
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const bool bb = (mk >> i) & 1u;
+                    const unsigned char* p = row_ptr(k, zr, A::cb(i), A::cm(i)) + xc[k][1 - A::ca(i)];
+                    const T f = bb ? Fmt<Q, S>::ld_delta(own, 0, opp<Q>(i)) : Fmt<Q, S>::ld_delta(p, 0, i);
+                    rd += f;
+                    if (A::ca(i)) ja += T(A::ca(i)) * f;
+                    if (A::cb(i)) jb += T(A::cb(i)) * f;
+                    if (A::cm(i)) jm += T(A::cm(i)) * f;
+                    phi += bb ? Fmt<Q, S>::ld_delta(own, 1, opp<Q>(i)) : Fmt<Q, S>::ld_delta(p, 1, i);
+                    psi += bb ? Fmt<Q, S>::ld_delta(own, 2, opp<Q>(i)) : Fmt<Q, S>::ld_delta(p, 2, i);
+                }
+            }
+            const T rho = (mk & 1u) ? T(0) : (Fmt<Q, S>::PACKED ? T(1) + rd : rd);
+            sm[slot][0][h] = rho;
+            sm[slot][1][h] = phi;
+            sm[slot][2][h] = psi;
+            sk[slot][h] = mk;
+            const int hx = h % HW, hy = h / HW;
+            if (hx >= H && hx < H + TX && hy >= HB && hy < HB + TY) {
+                const int t = (hy - HB) * TX + (hx - H);
+                sj[js][0][t] = ja;
+                sj[js][1][t] = jb;
+                sj[js][2][t] = jm;
+                sj[js][3][t] = rd;
+            }
+        }
+    };
+
+    // G: ghost values of the solid nodes of plane q within the one-node halo
+    auto ghosts_plane = [&](int q) {
+        const int slot = modp(q, R);
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+            const int h = tid + k * NT;
+            if (h >= HN) break;
+            const int hx = h % HW, hy = h / HW;
+            if (hx < 1 || hx > HW - 2 || (D == 3 && (hy < 1 || hy > HH - 2))) continue;
+            const uint32_t mk = sk[slot][h];
+            if (!(mk & 1u)) continue;
+            T acc[3] = {T(0), T(0), T(0)};
+            int n = 0;
+#pragma unroll
+            for (int i = 1; i <= Lat<Q>::NAXIS; ++i) {  // neighbour s + e_i is fluid?
+                if ((mk >> opp<Q>(i)) & 1u) continue;
+                const int sn = modp(q + A::cm(i), R);
+                const int hn = h + A::cb(i) * HW + A::ca(i);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[c] += sm[sn][c][hn] - P.Gw[c];
+                ++n;
+            }
+            if (n == 0) {
+                const T r2 = T(1.4142135623730951);
+#pragma unroll
+                for (int i = Lat<Q>::NAXIS + 1; i < Q; ++i) {
+                    if ((mk >> opp<Q>(i)) & 1u) continue;
+                    const int sn = modp(q + A::cm(i), R);
+                    const int hn = h + A::cb(i) * HW + A::ca(i);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[c] += sm[sn][c][hn] - r2 * P.Gw[c];
+                    ++n;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sm[slot][c][h] = n > 0 ? acc[c] / T(n) : T(0);
+        }
+    };
+
+    double mr = 0.0, mp = 0.0, ms = 0.0;
+
+    moments_plane(M0 - 2);
+    moments_plane(M0 - 1);
+    moments_plane(M0);
+    moments_plane(M0 + 1);
+    __syncthreads();
+    ghosts_plane(M0 - 1);
+    ghosts_plane(M0);
+    __syncthreads();
+
+    const int c0 = (ty + HB) * HW + tx + H;  // this thread's tile node in the region
+    for (int m = M0; m < M1; ++m) {
+        moments_plane(m + 2);
+        __syncthreads();
+        ghosts_plane(m + 1);
+        __syncthreads();
+        const int s0 = modp(m, R);
+        const uint32_t mk = sk[s0][c0];
+        if (!active || (mk & 1u)) continue;
+
+        // ---- derivatives from the ring (ghost values on solid neighbours)
+        T X0[3], gA[3], gB[3], gM[3], lp[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            X0[c] = sm[s0][c][c0];
+            gA[c] = gB[c] = gM[c] = lp[c] = T(0);
+        }
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (opp<Q>(i) < i) continue;
+            const int sp = modp(m + A::cm(i), R), sn = modp(m - A::cm(i), R);
+            const int cp = c0 + A::cb(i) * HW + A::ca(i);
+            const int cn = c0 - A::cb(i) * HW - A::ca(i);
+            const T w = T(Lat<Q>::w(i));
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T xpv = sm[sp][c][cp], xnv = sm[sn][c][cn];
+                const T d = w * (xpv - xnv);
+                if (A::ca(i)) gA[c] += T(A::ca(i)) * d;
+                if (A::cb(i)) gB[c] += T(A::cb(i)) * d;
+                if (A::cm(i)) gM[c] += T(A::cm(i)) * d;
+                lp[c] += w * (xpv + xnv);
+            }
+        }
+        T grad[3][3], lap[3];
+        constexpr T wrest = T(1.0 - Lat<Q>::w(0));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lap[c] = T(6) * (lp[c] - wrest * X0[c]);
+            grad[c][0] = T(3) * gA[c];
+            if (D == 3) {
+                grad[c][1] = T(3) * gB[c];
+                grad[c][2] = T(3) * gM[c];
+            } else {
+                grad[c][1] = T(3) * gM[c];
+                grad[c][2] = T(0);
+            }
+        }
+        const int t = ty * TX + tx, js = modp(m, 4);
+        const T jA = sj[js][0][t], jB = sj[js][1][t], jM = sj[js][2][t], rdc = sj[js][3][t];
+        NodeEq<Q, T> E;
+        if (D == 3) E.setup(P, X0[0], jA, jB, jM, X0[1], X0[2], grad, lap);
+        else E.setup(P, X0[0], jA, jM, T(0), X0[1], X0[2], grad, lap);
+        mr += rho_total<Q, S>(rdc);
+        mp += (double)X0[1];
+        ms += (double)X0[2];
+
+        // ---- pulled populations (bounce-back at solid sources)
+        const int zr[3] = {wrap1(m - 1, g.NM), m, wrap1(m + 1, g.NM)};
+        const unsigned char* own = own_row(zr, 0, 0) + xo[1];
+        T fv[Q], gv[Q], kv[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const bool bb = (mk >> i) & 1u;
+            const unsigned char* p = own_row(zr, A::cb(i), A::cm(i)) + xo[1 - A::ca(i)];
+            fv[i] = bb ? Fmt<Q, S>::ld(own, 0, opp<Q>(i)) : Fmt<Q, S>::ld(p, 0, i);
+            gv[i] = bb ? Fmt<Q, S>::ld(own, 1, opp<Q>(i)) : Fmt<Q, S>::ld(p, 1, i);
+            kv[i] = bb ? Fmt<Q, S>::ld(own, 2, opp<Q>(i)) : Fmt<Q, S>::ld(p, 2, i);
+        }
+
+        // ---- collide + store (same arithmetic as k_fused)
+        unsigned char* out = reinterpret_cast<unsigned char*>(dst) + ((long long)m * g.NB + yo[1]) * g.rowstride + xo[1];
+        const T cf = T(1) - P.omega[0], cg = T(1) - P.omega[1], ck = T(1) - P.omega[2];
+        const T Bf = P.omega[0] * E.bf, Rf = T(4.5) * P.omega[0] * E.rho, Of = T(3) * P.omega[0] * E.rho;
+        const T Bg = P.omega[1] * E.bg, Rg = T(4.5) * P.omega[1] * E.phi, Og = T(3) * P.omega[1] * E.phi;
+        const T Bk = P.omega[2] * E.bk, Rk = T(4.5) * P.omega[2] * E.psi, Ok = T(3) * P.omega[2] * E.psi;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) E.Gs[c] *= P.omega[0];
+        T sf = T(0), sg = T(0), sk2 = T(0), qf = T(0), qg = T(0), qk = T(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int o = opp<Q>(i);
+            if (o < i) continue;
+            const T w = T(Lat<Q>::w(i));
+            const T e = E.eu(i);
+            const T e2 = e * e;
+            const T evf = w * (Bf + Rf * e2) + E.grad_term(i), odf = (w * Of) * e;
+            const T evg = w * (Bg + Rg * e2), odg = (w * Og) * e;
+            const T evk = w * (Bk + Rk * e2), odk = (w * Ok) * e;
+            sf += T(2) * evf;
+            sg += T(2) * evg;
+            sk2 += T(2) * evk;
+            const T v[6] = {cf * fv[i] + (evf + odf), cf * fv[o] + (evf - odf),
+                            cg * gv[i] + (evg + odg), cg * gv[o] + (evg - odg),
+                            ck * kv[i] + (evk + odk), ck * kv[o] + (evk - odk)};
+            Fmt<Q, S>::st(out, 0, i, v[0]);
+            Fmt<Q, S>::st(out, 0, o, v[1]);
+            Fmt<Q, S>::st(out, 1, i, v[2]);
+            Fmt<Q, S>::st(out, 1, o, v[3]);
+            Fmt<Q, S>::st(out, 2, i, v[4]);
+            Fmt<Q, S>::st(out, 2, o, v[5]);
+            if (Fmt<Q, S>::PACKED) {
+                qf += Fmt<Q, S>::qdelta(0, i, v[0]) + Fmt<Q, S>::qdelta(0, o, v[1]);
+                qg += Fmt<Q, S>::qdelta(1, i, v[2]) + Fmt<Q, S>::qdelta(1, o, v[3]);
+                qk += Fmt<Q, S>::qdelta(2, i, v[4]) + Fmt<Q, S>::qdelta(2, o, v[5]);
+            }
+        }
+        if (Fmt<Q, S>::PACKED) {
+            Fmt<Q, S>::st_delta(out, 0, 0, rdc - qf);
+            Fmt<Q, S>::st_delta(out, 1, 0, E.phi - qg);
+            Fmt<Q, S>::st_delta(out, 2, 0, E.psi - qk);
+        } else {
+            Fmt<Q, S>::st(out, 0, 0, cf * fv[0] + (P.omega[0] * E.rho - sf));
+            Fmt<Q, S>::st(out, 1, 0, cg * gv[0] + (P.omega[1] * E.phi - sg));
+            Fmt<Q, S>::st(out, 2, 0, ck * kv[0] + (P.omega[2] * E.psi - sk2));
+        }
+    }
+
+    block_sum3(mr, mp, ms);
+    if (tid == 0) {
+        partials[3 * blockIdx.x + 0] = mr;
+        partials[3 * blockIdx.x + 1] = mp;
+        partials[3 * blockIdx.x + 2] = ms;
+    }
+}
+
 // ------------------------------------------------------------ host side
 
 // tile variants: 0 = default (D3Q19 32x4, D2Q9 128); D3Q19: 1 = 32x8, 2 = 64x4, 3 = 32x4;
@@ -360,7 +679,12 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
     const int variant = dbl ? 0 : (d.tile & 15);
     int mc = d.tile >> 8;
     FusedCfg<Q> c{};
-    if (Q == 19 && dbl) {
+    if (d.solid) {
+        // solid-aware kernel: a fixed tile per lattice (D3Q19 in double: 16x4 keeps
+        // its five-plane rings under the 48 KB static shared-memory limit)
+        c.TX = Q == 19 ? (dbl ? 16 : 32) : 128;
+        c.TY = Q == 19 ? 4 : 1;
+    } else if (Q == 19 && dbl) {
         c.TX = 16;  // double storage: a smaller tile keeps the static shared ring small
         c.TY = 8;
     } else if (Q == 19) {
@@ -394,7 +718,7 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
 
 template <int Q, typename S>
 inline bool fused_supported(const tlbm_host::DevState& d) {
-    return d.solid == nullptr;
+    return d.solid == nullptr || d.nbm != nullptr;
 }
 
 template <int Q, typename S>
@@ -436,6 +760,23 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
     if (nb > 0x7fffffffLL || nb > d.partials_cap) return cudaErrorInvalidConfiguration;
     const S* src = static_cast<const S*>(d.pop[d.cur]);
     S* dst = static_cast<S*>(d.pop[1 - d.cur]);
+    if (d.solid) {
+        if (!d.nbm_ready) {
+            const Geom gg{d.nx, d.ny, d.nz, d.N, d.Np, d.ncx};
+            k_nbmask<Q><<<1216, 256, 0, st>>>(gg, d.solid, d.nbm);
+            d.nbm_ready = 1;
+        }
+        auto gos = [&](auto kern, int threads) {
+            kern<<<(int)nb, threads, 0, st>>>(g, src, dst, d.nbm, P, d.partials);
+        };
+        if constexpr (Q == 19) {
+            if constexpr (sizeof(S) == 8) gos(k_fused_solid<Q, S, 16, 4>, 64);
+            else gos(k_fused_solid<Q, S, 32, 4>, 128);
+        } else {
+            gos(k_fused_solid<Q, S, 128, 1>, 128);
+        }
+        return cudaGetLastError();
+    }
     auto go = [&](auto kern, int threads) { kern<<<(int)nb, threads, 0, st>>>(g, src, dst, P, d.partials); };
     if constexpr (sizeof(S) == 8) {
         // double storage is the parity path: one tile shape per lattice

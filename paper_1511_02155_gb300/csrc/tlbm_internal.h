@@ -29,6 +29,8 @@ struct DevState {
     void* pop[2];        // A-B population buffers (chunk layout, see tlbm_lattice.cuh)
     int cur;             // buffer holding the current state
     const uint8_t* solid;  // device mask (nullptr when there are no solid nodes)
+    uint32_t* nbm;       // per-node neighbour-solid bits for the fused step (with solids)
+    int nbm_ready;       // nbm has been built
     void* mom;           // split-step moment arrays [3][Np] (compute type); scratch
     double* partials;    // mass partial sums, 3 per block
     double* step_mass;   // [3] totals accumulated inside the last step

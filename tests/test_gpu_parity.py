@@ -108,27 +108,30 @@ def test_fp64_parity_periodic(Q, shape, kernel):
     _compare_fp64(eng, p, pops)
 
 
-def test_fp64_parity_walls_and_wetting_d2q9():
+@pytest.mark.parametrize("kernel", ["fused", "split"])
+def test_fp64_parity_walls_and_wetting_d2q9(kernel):
     C, solid = W.sessile_drop(40, 30, 8.0, m=2, n=0)
     h = (0.0005, -0.0008, 0.001)
-    eng, p, pops = _setup(9, (40, 30, 1), C, "fp64", solid=solid, h=h)
-    assert eng.kernel == "split"
+    eng, p, pops = _setup(9, (40, 30, 1), C, "fp64", kernel, solid=solid, h=h)
+    assert eng.kernel == kernel
     _compare_fp64(eng, p, pops, solid=solid, tol=1e-13)
     eng.step(150)
     oracle.step(p, *pops, 150, solid)
     _compare_fp64(eng, p, pops, solid=solid)
 
 
-def test_fp64_parity_square_well_with_corners():
+@pytest.mark.parametrize("kernel", ["fused", "split"])
+def test_fp64_parity_square_well_with_corners(kernel):
     C, solid = W.square_well(48, 40, width=14, depth=10, floor=6)
     h = (-0.0006, 0.0009, 0.0004)
-    eng, p, pops = _setup(9, (48, 40, 1), C, "fp64", solid=solid, h=h, kappa=(0.01, 0.012, 0.015))
+    eng, p, pops = _setup(9, (48, 40, 1), C, "fp64", kernel, solid=solid, h=h, kappa=(0.01, 0.012, 0.015))
     eng.step(120)
     oracle.step(p, *pops, 120, solid)
     _compare_fp64(eng, p, pops, solid=solid)
 
 
-def test_fp64_parity_walls_d3q19():
+@pytest.mark.parametrize("kernel", ["fused", "split"])
+def test_fp64_parity_walls_d3q19(kernel):
     nx, ny, nz = 12, 10, 9
     solid = np.zeros((nz, ny, nx), np.uint8)
     solid[:, 0, :] = 1
@@ -136,7 +139,7 @@ def test_fp64_parity_walls_d3q19():
     solid[3:6, 1:3, 4:7] = 1  # a block on the bottom wall (edges and corners)
     C = W.spinodal((nz, ny, nx), seed=5, amp=0.2)
     h = (0.0004, -0.0006, 0.0002)
-    eng, p, pops = _setup(19, (nx, ny, nz), C, "fp64", solid=solid, h=h)
+    eng, p, pops = _setup(19, (nx, ny, nz), C, "fp64", kernel, solid=solid, h=h)
     eng.step(40)
     oracle.step(p, *pops, 40, solid.reshape(-1))
     _compare_fp64(eng, p, pops, solid=solid.reshape(-1))
@@ -169,10 +172,11 @@ def test_fp32_spinodal_3d_against_fp64_oracle(kernel):
         assert np.abs(got[name] - want).max() <= 1e-4, name
 
 
-def test_fp32_walls_against_fp64_oracle():
+@pytest.mark.parametrize("kernel", ["fused", "split"])
+def test_fp32_walls_against_fp64_oracle(kernel):
     C, solid = W.sessile_drop(64, 40, 12.0, m=2, n=0)
     h = (0.0004, -0.0006, 0.0008)
-    eng, p, pops = _setup(9, (64, 40, 1), C, "fp32", solid=solid, h=h)
+    eng, p, pops = _setup(9, (64, 40, 1), C, "fp32", kernel, solid=solid, h=h)
     eng.step(500)
     oracle.step(p, *pops, 500, solid)
     C1, C2, C3, _, _ = oracle.fields(p, *pops, solid)
@@ -294,6 +298,29 @@ def test_tile_variants_are_bitwise_identical():
         eng.close()
 
 
+@pytest.mark.parametrize("Q,shape", [(9, (150, 37, 1)), (19, (37, 13, 11))])
+def test_fused_walls_ragged_fp64(Q, shape):
+    """Solid geometry on lattices that are ragged against every tile: walls, a
+    block with edges and corners, and wetting on all three fluids."""
+    nx, ny, nz = shape
+    sh = (ny, nx) if Q == 9 else (nz, ny, nx)
+    solid = np.zeros(sh, np.uint8)
+    if Q == 9:
+        solid[0, :] = 1
+        solid[ny - 1, :] = 1
+        solid[1:6, 20:31] = 1
+    else:
+        solid[:, 0, :] = 1
+        solid[:, ny - 1, :] = 1
+        solid[2:6, 1:4, 10:17] = 1
+    C = W.spinodal(sh, seed=12, amp=0.2)
+    h = (0.0006, -0.0004, 0.0003)
+    eng, p, pops = _setup(Q, shape, C, "fp64", "fused", solid=solid, h=h)
+    eng.step(30)
+    oracle.step(p, *pops, 30, solid.reshape(-1))
+    _compare_fp64(eng, p, pops, solid=solid.reshape(-1))
+
+
 def test_fused_and_split_agree_fp32():
     C = W.lens(64, 48, 10.0, 1.0, 12.0, 36.0, (32.0, 36.0))
     out = []
@@ -385,6 +412,6 @@ def test_launch_counts():
     assert eng.launches_per_step == 3
     solid = W.walls_y(32, 24)
     eng2, _, _ = _setup(9, (32, 24, 1), C, "fp32", solid=solid)
-    assert eng2.kernel == "split" and eng2.launches_per_step == 4
-    with pytest.raises(tl.TLBMError):
-        eng2.set_kernel("fused")
+    assert eng2.kernel == "fused" and eng2.launches_per_step == 2
+    eng2.set_kernel("split")
+    assert eng2.launches_per_step == 4
