@@ -57,6 +57,10 @@ def workload(name: str, size: int = 0):
     if name == "probe8192":
         n = size or 8192
         return W.probe_2d(n), f"D2Q9 {n}^2 periodic ternary spinodal mixture"
+    if name == "wells4096":
+        nx = size or 4096
+        return (W.wells_2d(nx, nx // 2),
+                f"D2Q9 {nx}x{nx // 2} walls with 32 square wells, wetting on all fluids")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -159,6 +163,7 @@ def cpu_baseline(cfg_name: str, cfg: dict, budget_s: float = 12.0):
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     import oracle
     Q = cfg["Q"]
+    solid = None
     if Q == 19:
         n = 48
         C = W.spinodal((n, n, n), seed=3)
@@ -166,21 +171,30 @@ def cpu_baseline(cfg_name: str, cfg: dict, budget_s: float = 12.0):
         sample = f"D3Q19 {n}^3 sub-lattice of the same spinodal recipe"
     else:
         ny, nx = (128, 256) if cfg_name == "lens512" else (256, 256)
+        solid = None
         if cfg_name == "lens512":
             C = W.lens(nx, ny, 30.0, 1.0, 0.0, 64.0, (128.0, 64.0))
+        elif cfg_name == "wells4096":
+            wc = W.wells_2d(nx, ny, 2)
+            C, solid = wc["C"], wc["solid"]
         else:
             C = W.spinodal((ny, nx), seed=5)
         shape = (nx, ny, 1)
         sample = f"D2Q9 {nx}x{ny} sub-lattice of the same recipe"
-    p = oracle.make_params(Q, *shape, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"], cfg["M_psi"])
-    f, g, k = oracle.init_equilibrium(p, *W.to_aux(*C))
+    p = oracle.make_params(Q, *shape, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"], cfg["M_psi"],
+                           cfg.get("h", (0.0, 0.0, 0.0)))
+    rho, phi, psi = W.to_aux(*C)
+    if solid is not None:
+        for a in (rho, phi, psi):
+            a[solid != 0] = 0.0
+    f, g, k = oracle.init_equilibrium(p, rho, phi, psi, solid=solid)
     N = int(np.prod(shape))
     t0 = time.perf_counter()
-    oracle.step(p, f, g, k, 1)
+    oracle.step(p, f, g, k, 1, solid)
     one = time.perf_counter() - t0
     nsteps = max(1, int(budget_s / max(one, 1e-6)))
     t0 = time.perf_counter()
-    oracle.step(p, f, g, k, nsteps)
+    oracle.step(p, f, g, k, nsteps, solid)
     dt = time.perf_counter() - t0
     return {"value": round(N * nsteps / dt / 1e6, 4), "unit": "MLUPS",
             "cores": int(os.environ.get("OMP_NUM_THREADS", cores)), "kind": "oracle",
@@ -247,7 +261,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="spinodal256", choices=["spinodal256", "lens512", "probe8192"])
+    ap.add_argument("--workload", default="spinodal256", choices=["spinodal256", "lens512", "probe8192", "wells4096"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "split"])
     ap.add_argument("--tile", default="0,0")
@@ -283,8 +297,12 @@ def main():
         cfg["C"] = W.spinodal((nz, ny, nx), seed=3 + rank)  # an independent replica per rank
     rho, phi, psi = W.to_aux(*cfg["C"])
     cfg["C"] = None
+    solid = cfg.get("solid")
+    if solid is not None:
+        for a in (rho, phi, psi):
+            a[solid != 0] = 0.0
     eng = tl.TernaryLB(Q, nx, ny, nz, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"],
-                       cfg["M_psi"], cfg["h"], None, args.precision)
+                       cfg["M_psi"], cfg["h"], solid, args.precision)
     if args.kernel != "auto":
         eng.set_kernel(args.kernel)
     tv, tc = (int(v) for v in args.tile.split(","))
@@ -323,7 +341,10 @@ def main():
     eng.set_timing(False)
     kernel_ms = kms / max(ksteps, 1)
     bpn = bytes_per_node(Q, args.precision)
-    alg_bytes = bpn * N  # every population read once and written once
+    n_fluid = N if solid is None else int(N - np.count_nonzero(solid))
+    # every population of a fluid node read once and written once, plus one mask
+    # byte per node where solid nodes exist
+    alg_bytes = bpn * n_fluid + (0 if solid is None else N)
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     kind = eng.kernel
@@ -356,7 +377,8 @@ def main():
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-store/f32",
                                            "bf16": "bf16-store/f32"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": label, "nodes_per_gpu": N, "lattice": f"D{3 if Q == 19 else 2}Q{Q}",
+            "config": {"workload": label, "nodes_per_gpu": N, "fluid_nodes_per_gpu": n_fluid,
+                       "lattice": f"D{3 if Q == 19 else 2}Q{Q}",
                        "precision": args.precision, "kernel": kind,
                        "l2": "populations exceed L2 (no flush needed)" if alg_bytes / 2 > 129e6
                        else "L2-resident lattice", "parallelism": f"replicas x{world}"},

@@ -453,15 +453,17 @@ k_fused_solid(MGeom g, const S* __restrict__ src, S* __restrict__ dst, const uin
                 const unsigned char* own = row_ptr(k, zr, 0, 0) + xc[k][1];
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
-                    const bool bb = (mk >> i) & 1u;
+                    // pull source, or this node's opposite run when the source is solid:
+                    // one pointer select, then loads at the run offsets of direction i
                     const unsigned char* p = row_ptr(k, zr, A::cb(i), A::cm(i)) + xc[k][1 - A::ca(i)];
-                    const T f = bb ? Fmt<Q, S>::ld_delta(own, 0, opp<Q>(i)) : Fmt<Q, S>::ld_delta(p, 0, i);
+                    if (i > 0 && ((mk >> i) & 1u)) p = own + Fmt<Q, S>::run_gap(i, opp<Q>(i));
+                    const T f = Fmt<Q, S>::ld_delta(p, 0, i);
                     rd += f;
                     if (A::ca(i)) ja += T(A::ca(i)) * f;
                     if (A::cb(i)) jb += T(A::cb(i)) * f;
                     if (A::cm(i)) jm += T(A::cm(i)) * f;
-                    phi += bb ? Fmt<Q, S>::ld_delta(own, 1, opp<Q>(i)) : Fmt<Q, S>::ld_delta(p, 1, i);
-                    psi += bb ? Fmt<Q, S>::ld_delta(own, 2, opp<Q>(i)) : Fmt<Q, S>::ld_delta(p, 2, i);
+                    phi += Fmt<Q, S>::ld_delta(p, 1, i);
+                    psi += Fmt<Q, S>::ld_delta(p, 2, i);
                 }
             }
             const T rho = (mk & 1u) ? T(0) : (Fmt<Q, S>::PACKED ? T(1) + rd : rd);
@@ -593,11 +595,11 @@ k_fused_solid(MGeom g, const S* __restrict__ src, S* __restrict__ dst, const uin
         T fv[Q], gv[Q], kv[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const bool bb = (mk >> i) & 1u;
             const unsigned char* p = own_row(zr, A::cb(i), A::cm(i)) + xo[1 - A::ca(i)];
-            fv[i] = bb ? Fmt<Q, S>::ld(own, 0, opp<Q>(i)) : Fmt<Q, S>::ld(p, 0, i);
-            gv[i] = bb ? Fmt<Q, S>::ld(own, 1, opp<Q>(i)) : Fmt<Q, S>::ld(p, 1, i);
-            kv[i] = bb ? Fmt<Q, S>::ld(own, 2, opp<Q>(i)) : Fmt<Q, S>::ld(p, 2, i);
+            if (i > 0 && ((mk >> i) & 1u)) p = own + Fmt<Q, S>::run_gap(i, opp<Q>(i));
+            fv[i] = Fmt<Q, S>::ld(p, 0, i);
+            gv[i] = Fmt<Q, S>::ld(p, 1, i);
+            kv[i] = Fmt<Q, S>::ld(p, 2, i);
         }
 
         // ---- collide + store (same arithmetic as k_fused)

@@ -181,6 +181,9 @@ struct Fmt {
         return PACKED ? (i == 0 ? (3 * (Q - 1) + 2 * s) * 32 * 2 : (s * (Q - 1) + i - 1) * 32 * 2)
                       : (s * Q + i) * 32 * ESZ;
     }
+    // byte distance from the run of (s, i) to the run of (s, j) -- the same for
+    // every set s when i, j >= 1
+    __host__ __device__ static constexpr int run_gap(int i, int j) { return off(0, j) - off(0, i); }
     // rest-state value subtracted before storage (packed formats, set f)
     __host__ __device__ static constexpr double bias(int s, int i) {
         return (PACKED && s == 0) ? Lat<Q>::w(i) : 0.0;

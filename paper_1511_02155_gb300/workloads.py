@@ -248,3 +248,35 @@ def probe_2d(n: int = 8192, seed: int = 5):
     C = spinodal((n, n), seed)
     return dict(Q=9, nx=n, ny=n, nz=1, kappa=(0.01, 0.01, 0.01), alpha=1.0, tau_f=0.8,
                 M_phi=0.1, M_psi=0.1, h=(0.0, 0.0, 0.0), C=C, solid=None)
+
+
+def wells_2d(nx: int = 4096, ny: int = 2048, nwells: int = 32, seed: int = 4):
+    """Wall-bounded D2Q9 lattice for timing the wetting path: solid floor
+    (8 rows) and lid (1 row), ``nwells`` square wells of seeded width and depth
+    cut into the floor block, each holding a fluid-3 drop; fluid 1 below a flat
+    1/2 interface at mid-height, fluid 2 above.  Wetting h = (0.0004, -0.0004,
+    0.0002) with kappa = (0.01, 0.01, 0.01)."""
+    rng = uniform(seed, 2 * nwells)
+    floor, block = 8, 40
+    solid = np.zeros((ny, nx), dtype=np.uint8)
+    solid[:floor + block, :] = 1
+    solid[ny - 1, :] = 1
+    pitch = nx // nwells
+    x, y = _grid2(nx, ny)
+    C3 = np.zeros((ny, nx))
+    for k in range(nwells):
+        w = int(20 + 60 * rng[2 * k])
+        dpt = int(10 + 30 * rng[2 * k + 1])
+        x0 = k * pitch + (pitch - w) // 2
+        y0 = floor + block - dpt
+        solid[y0:floor + block, x0:x0 + w] = 0
+        inwell = (x >= x0) & (x < x0 + w) & (y >= y0) & (y < floor + block)
+        C3 = np.where(inwell, profile(floor + block - 0.5 - y, 1.0), C3)
+    y_if = floor + block + (ny - 1 - floor - block) / 2
+    B = profile(y_if - y, 1.0)
+    C1 = (1 - C3) * B
+    C2 = (1 - C3) * (1 - B)
+    for c in (C1, C2, C3):
+        c[solid != 0] = 0.0
+    return dict(Q=9, nx=nx, ny=ny, nz=1, kappa=(0.01, 0.01, 0.01), alpha=1.0, tau_f=1.0,
+                M_phi=0.1, M_psi=0.1, h=(0.0004, -0.0004, 0.0002), C=[C1, C2, C3], solid=solid)
