@@ -124,10 +124,12 @@ tlbm_kernel tlbm_get_kernel(const tlbm *t);
 /* Tile of the fused step.  variant = shape | mode << 4: shape 0 = default
  * (D3Q19 32x4, D2Q9 128 nodes), D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4 nodes
  * per block; D2Q9 1 = 128, 2 = 256, 3 = 64 nodes per row.  mode selects the
- * load order inside a plane (0 default for the lattice; 1 interleaved halo
- * loads; 2 collision operands loaded first; 3 both; 4 per-warp L2 prefetch
- * three planes ahead; 5 = 1 + 4; 6 plain order; not every mode is built for
- * every shape, the others fall back to the shape's default).
+ * load order and cache hints inside a plane (0 default for the lattice and
+ * storage; 1 interleaved halo loads; 2 collision operands loaded first; 3 both;
+ * 4 per-warp L2 prefetch three planes ahead; 5 = 1 + 4; 6 plain order;
+ * 8 evict-first stores; 9 also evict-first collision loads; 12, 13 = 8, 9 with
+ * the prefetch; a mode not built for a shape falls back to its default; the
+ * variant must be below 256).
  * chunk = planes marched per block (0 = chosen from the lattice size).  Double
  * storage ignores the choice.  Results do not depend on the tile. */
 tlbm_status tlbm_set_tile(tlbm *t, int variant, int chunk);

@@ -293,7 +293,7 @@ tlbm_kernel tlbm_get_kernel(const tlbm* t) {
 // Tile choice of the fused step: variant (0 = default) and planes per chunk (0 = auto).
 tlbm_status tlbm_set_tile(tlbm* t, int variant, int chunk) {
     if (!t) return TLBM_ERR_ARG;
-    if (variant < 0 || variant > 127 || (variant & 15) > 3 || chunk < 0 || chunk > 4096)
+    if (variant < 0 || variant > 255 || (variant & 15) > 3 || chunk < 0 || chunk > 4096)
         return fail(t, TLBM_ERR_ARG, "bad tile");
     t->d.tile = variant + 256 * chunk;
     // partial sums must fit: blocks grow as chunks shrink

@@ -63,7 +63,9 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // ILP: a thread's border node loads interleave with its own node's loads.
 // EARLY: phase C's loads are issued before phase M's (values held across M).
 // PF: each warp prefetches its own 32-node chunk three planes ahead into L2.
-template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false>
+// HINT: 1 streams the stores out (evict-first); 2 also marks phase C's loads,
+//       the last use of those lines, evict-first.
+template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false, int HINT = 0>
 __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))  // 16 warps per SM
 k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename Store<S>::T> P,
         double* __restrict__ partials) {
@@ -205,9 +207,15 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const unsigned char* pi = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
-                fv[i] = Fmt<Q, S>::ld(pi, 0, i);
-                gv[i] = Fmt<Q, S>::ld(pi, 1, i);
-                kv[i] = Fmt<Q, S>::ld(pi, 2, i);
+                if (HINT >= 2) {
+                    fv[i] = Fmt<Q, S>::ld_last(pi, 0, i);
+                    gv[i] = Fmt<Q, S>::ld_last(pi, 1, i);
+                    kv[i] = Fmt<Q, S>::ld_last(pi, 2, i);
+                } else {
+                    fv[i] = Fmt<Q, S>::ld(pi, 0, i);
+                    gv[i] = Fmt<Q, S>::ld(pi, 1, i);
+                    kv[i] = Fmt<Q, S>::ld(pi, 2, i);
+                }
             }
         };
         if (EARLY && active) load_node();
@@ -271,6 +279,10 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
             unsigned char* out = reinterpret_cast<unsigned char*>(dst) +
                                  ((long long)m * g.NB + yb[0][1]) * g.rowstride + xc[0][1];
 
+            auto st_ = [&](unsigned char* o, int ss, int ii, T v) {
+                if (HINT >= 1) Fmt<Q, S>::st_stream(o, ss, ii, v);
+                else Fmt<Q, S>::st(o, ss, ii, v);
+            };
             // BGK with omega folded into the equilibria: x* = (1 - omega) x + omega x_eq,
             // and omega x_eq = EV +- OD for a pair of opposite links, where
             // EV = w (B + R (e.u)^2) [+ gradient terms for f] and OD = w O (e.u)
@@ -298,12 +310,12 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
                 const T v[6] = {cf * fv[i] + (evf + odf), cf * fv[o] + (evf - odf),
                                 cg * gv[i] + (evg + odg), cg * gv[o] + (evg - odg),
                                 ck * kv[i] + (evk + odk), ck * kv[o] + (evk - odk)};
-                Fmt<Q, S>::st(out, 0, i, v[0]);
-                Fmt<Q, S>::st(out, 0, o, v[1]);
-                Fmt<Q, S>::st(out, 1, i, v[2]);
-                Fmt<Q, S>::st(out, 1, o, v[3]);
-                Fmt<Q, S>::st(out, 2, i, v[4]);
-                Fmt<Q, S>::st(out, 2, o, v[5]);
+                st_(out, 0, i, v[0]);
+                st_(out, 0, o, v[1]);
+                st_(out, 1, i, v[2]);
+                st_(out, 1, o, v[3]);
+                st_(out, 2, i, v[4]);
+                st_(out, 2, o, v[5]);
                 if (Fmt<Q, S>::PACKED) {
                     qf += Fmt<Q, S>::qdelta(0, i, v[0]) + Fmt<Q, S>::qdelta(0, o, v[1]);
                     qg += Fmt<Q, S>::qdelta(1, i, v[2]) + Fmt<Q, S>::qdelta(1, o, v[3]);
@@ -318,9 +330,9 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
                 Fmt<Q, S>::st_delta(out, 2, 0, E.psi - qk);
             } else {
                 // omega x_eq_0 = omega X - sum of omega x_eq over the moving links
-                Fmt<Q, S>::st(out, 0, 0, cf * fv[0] + (P.omega[0] * E.rho - sf));
-                Fmt<Q, S>::st(out, 1, 0, cg * gv[0] + (P.omega[1] * E.phi - sg));
-                Fmt<Q, S>::st(out, 2, 0, ck * kv[0] + (P.omega[2] * E.psi - sk));
+                st_(out, 0, 0, cf * fv[0] + (P.omega[0] * E.rho - sf));
+                st_(out, 1, 0, cg * gv[0] + (P.omega[1] * E.phi - sg));
+                st_(out, 2, 0, ck * kv[0] + (P.omega[2] * E.psi - sk));
             }
         }
         jc[0] = jn[0];
@@ -671,9 +683,10 @@ struct FusedCfg {
 // d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 32x4,
 // D2Q9 128); D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4; D2Q9 1 = 128, 2 = 256,
 // 3 = 64.  mode bit 0: interleaved border loads; bit 1: early phase-C loads;
-// bit 2: per-warp L2 prefetch three planes ahead.  mode 0 is the default for
-// the shape and format (D3Q19 32x4: plain for FP32, 4 for 16-bit storage;
-// other D3Q19: 1; D2Q9: 4); 6 selects the plain loop.  chunk = planes
+// bit 2: per-warp L2 prefetch three planes ahead; 8 / 9: evict-first stores /
+// stores and collision loads (12, 13 with the prefetch).  mode 0 is the
+// default for the shape and format (D3Q19 32x4: 8 for FP32, 12 for 16-bit
+// storage; other D3Q19: 1; D2Q9: 13); 6 selects the plain loop.  chunk = planes
 // per block (0 = chosen from the lattice size).
 template <int Q>
 inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
@@ -698,13 +711,13 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
         c.TX = v == 2 ? 256 : (v == 3 ? 64 : 128);
         c.TY = 1;
     }
-    c.mode = dbl ? 0 : ((d.tile >> 4) & 7);
-    // defaults measured on GB300: D3Q19 32x4 plain loop for 4-byte storage and
+    c.mode = dbl ? 0 : ((d.tile >> 4) & 15);
+    // defaults measured on GB300: D3Q19 32x4 with evict-first stores, plus a
     // per-warp L2 prefetch for the 16-bit formats (a plane of FP32 populations
     // is too large for the prefetch to stay in L2); 64x4 and 32x8 interleaved
-    // border loads; D2Q9 per-warp L2 prefetch three planes ahead
+    // border loads; D2Q9 prefetch, evict-first stores and collision loads
     if (c.mode == 0)
-        c.mode = (Q == 19) ? (c.TX == 32 && c.TY == 4 ? (d.prec >= 2 ? 4 : 6) : 1) : 4;
+        c.mode = (Q == 19) ? (c.TX == 32 && c.TY == 4 ? (d.prec >= 2 ? 12 : 8) : 1) : 13;
     const int NA = d.nx;
     const int NB = (Q == 19) ? d.ny : 1;
     const int NM = (Q == 19) ? d.nz : d.ny;
@@ -797,6 +810,10 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
             switch (c.mode) {
                 case 1: go(k_fused<Q, S, 32, 4, true, false>, 128); break;
                 case 4: go(k_fused<Q, S, 32, 4, false, false, true>, 128); break;
+                case 8: go(k_fused<Q, S, 32, 4, false, false, false, 1>, 128); break;
+                case 9: go(k_fused<Q, S, 32, 4, false, false, false, 2>, 128); break;
+                case 12: go(k_fused<Q, S, 32, 4, false, false, true, 1>, 128); break;
+                case 13: go(k_fused<Q, S, 32, 4, false, false, true, 2>, 128); break;
                 default: go(k_fused<Q, S, 32, 4, false, false>, 128);
             }
         } else {
@@ -815,6 +832,10 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
             go(k_fused<Q, S, 64, 1, false, false>, 64);
         } else if (c.mode == 4) {
             go(k_fused<Q, S, 128, 1, false, false, true>, 128);
+        } else if (c.mode == 12) {
+            go(k_fused<Q, S, 128, 1, false, false, true, 1>, 128);
+        } else if (c.mode == 13) {
+            go(k_fused<Q, S, 128, 1, false, false, true, 2>, 128);
         } else {
             go(k_fused<Q, S, 128, 1, false, false>, 128);  // plain loop
         }

@@ -205,6 +205,34 @@ struct Fmt {
     static __device__ __forceinline__ T ld(const unsigned char* n, int s, int i) {
         return ld_delta(n, s, i) + T(bias(s, i));
     }
+    // the same, marking the line evict-first (its last use in this kernel)
+    static __device__ __forceinline__ T ld_last(const unsigned char* n, int s, int i) {
+        if constexpr (PACKED) {
+            if (i == 0) {
+                const unsigned lo = __ldcs(reinterpret_cast<const unsigned short*>(n + off(s, 0)));
+                const unsigned hi = __ldcs(reinterpret_cast<const unsigned short*>(n + off(s, 0) + 64));
+                return __uint_as_float(lo | (hi << 16)) + T(bias(s, 0));
+            }
+            return Store<S>::get(__ldcs(reinterpret_cast<const S*>(n + off(s, i)))) + T(bias(s, i));
+        } else {
+            return __ldcs(reinterpret_cast<const S*>(n + off(s, i)));
+        }
+    }
+    // store with an evict-first hint (streamed out, read only by the next step)
+    static __device__ __forceinline__ void st_stream(unsigned char* n, int s, int i, T v) {
+        if constexpr (PACKED) {
+            const T d = v - T(bias(s, i));
+            if (i == 0) {
+                const unsigned u = __float_as_uint(d);
+                __stcs(reinterpret_cast<unsigned short*>(n + off(s, 0)), (unsigned short)(u & 0xffffu));
+                __stcs(reinterpret_cast<unsigned short*>(n + off(s, 0) + 64), (unsigned short)(u >> 16));
+            } else {
+                __stcs(reinterpret_cast<S*>(n + off(s, i)), Store<S>::put(d));
+            }
+        } else {
+            __stcs(reinterpret_cast<S*>(n + off(s, i)), v);
+        }
+    }
     // store the deviation d = x - bias of (s, i)
     static __device__ __forceinline__ void st_delta(unsigned char* n, int s, int i, T d) {
         if constexpr (PACKED) {
