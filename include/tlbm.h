@@ -243,6 +243,48 @@ tlbm_status tlbm_step_noalloc(tlbm_lattice lattice, tlbm_precision precision, in
                               double M_psi, const double h[3], const uint8_t *solid_dev,
                               const void *src_dev, void *dst_dev, double *mass_dev, void *cuda_stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent lattices of one lattice type and storage format (for example
+ * a contact-angle or kappa sweep over lattices of uneven size) advanced by ONE
+ * kernel launch per step plus one launch for all their FP64 totals.  A batch
+ * groups existing engines; each keeps its own state, parameters, solid mask and
+ * accessors (tlbm_fields, tlbm_mass, ...), and a batched step gives bit for bit
+ * the same populations as stepping each member alone with the same tile.
+ */
+typedef struct tlbm_batch tlbm_batch;
+
+/* Group count >= 1 engines: same device, stream, lattice and precision, all with
+ * or all without solid nodes, each at the same step parity (equal parity of
+ * steps taken since initialisation).  The members stay owned by the caller and
+ * must outlive the batch.  Returns TLBM_ERR_ARG if they do not match. */
+tlbm_status tlbm_batch_create(tlbm_batch **out, tlbm *const *members, int count);
+
+/* Advance every member by nsteps.  Fails with TLBM_ERR_ARG if a member was
+ * stepped alone since the last batched step (its parity differs). */
+tlbm_status tlbm_batch_step(tlbm_batch *b, int64_t nsteps);
+
+/* Tile for every member (tlbm_set_tile encoding).  On failure the previous tile
+ * stays in use. */
+tlbm_status tlbm_batch_set_tile(tlbm_batch *b, int variant, int chunk);
+
+/* Time candidate tiles (shape and planes per block) for trial_steps steps each
+ * with CUDA events on the members' stream, keep the fastest, and report it.
+ * The trial steps are real steps: every member advances by them. */
+tlbm_status tlbm_batch_autotune(tlbm_batch *b, int trial_steps, int *variant, int *chunk);
+
+/* on != 0: replay the steps as a CUDA graph of two batched steps (captured on
+ * a private stream at the next tlbm_batch_step, launched on the members' stream). */
+tlbm_status tlbm_batch_set_graph(tlbm_batch *b, int on);
+
+/* Blocks of one batched step launch. */
+int64_t tlbm_batch_blocks(const tlbm_batch *b);
+
+/* Message of the last failed batch call ("" if none; NULL b: last create). */
+const char *tlbm_batch_last_error(const tlbm_batch *b);
+
+/* Release the batch (not its members). */
+void tlbm_batch_destroy(tlbm_batch *b);
+
 /* Message of the last failed tlbm_step_noalloc call on this host thread ("" if none). */
 const char *tlbm_noalloc_last_error(void);
 

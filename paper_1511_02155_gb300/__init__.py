@@ -20,7 +20,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["TernaryLB", "TLBMError", "load_library", "lib_path", "D2Q9", "D3Q19",
+__all__ = ["TernaryLB", "TernaryBatch", "TLBMError", "load_library", "lib_path", "D2Q9", "D3Q19",
            "FP64", "FP32", "FP16_OFFSET", "BF16_OFFSET", "KERNEL_AUTO", "KERNEL_FUSED",
            "KERNEL_SPLIT"]
 
@@ -82,6 +82,14 @@ def _declare(lib):
         "tlbm_launches_per_step": (i, [_H]),
         "tlbm_last_error": (ctypes.c_char_p, [_H]),
         "tlbm_status_string": (ctypes.c_char_p, [i]),
+        "tlbm_batch_create": (i, [ctypes.POINTER(_H), ctypes.POINTER(_H), i]),
+        "tlbm_batch_step": (i, [_H, i64]),
+        "tlbm_batch_set_tile": (i, [_H, i, i]),
+        "tlbm_batch_autotune": (i, [_H, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "tlbm_batch_set_graph": (i, [_H, i]),
+        "tlbm_batch_blocks": (i64, [_H]),
+        "tlbm_batch_last_error": (ctypes.c_char_p, [_H]),
+        "tlbm_batch_destroy": (None, [_H]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -286,3 +294,62 @@ class TernaryLB:
     def set_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         self._check(self._lib.tlbm_set_state(self._h, buf.ctypes.data_as(_vp), buf.size))
+
+
+class TernaryBatch:
+    """Many TernaryLB engines advanced together: one kernel launch per step.
+
+    Members must share lattice, precision, device and stream, and all have (or
+    all lack) solid nodes.  They stay usable on their own (fields, mass, ...);
+    stepping one alone breaks the batch's common parity until it has taken an
+    even number of lone steps.  The engines must outlive the batch.
+    """
+
+    def __init__(self, members):
+        self._lib = load_library()
+        self.members = list(members)
+        hs = (_H * len(self.members))(*[m._h.value for m in self.members])
+        self._h = _H()
+        rc = self._lib.tlbm_batch_create(ctypes.byref(self._h), hs, len(self.members))
+        if rc != 0:
+            raise TLBMError(rc, self._lib.tlbm_batch_last_error(None).decode())
+
+    def _check(self, rc):
+        if rc != 0:
+            raise TLBMError(rc, self._lib.tlbm_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.tlbm_batch_destroy(self._h)
+            self._h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def step(self, n=1):
+        self._check(self._lib.tlbm_batch_step(self._h, int(n)))
+
+    def set_tile(self, variant=0, chunk=0):
+        self._check(self._lib.tlbm_batch_set_tile(self._h, int(variant), int(chunk)))
+
+    def set_graph(self, on=True):
+        self._check(self._lib.tlbm_batch_set_graph(self._h, 1 if on else 0))
+
+    def autotune(self, trial_steps=10):
+        """Pick the fastest tile; every member advances by the trial steps."""
+        v, c = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.tlbm_batch_autotune(self._h, int(trial_steps), ctypes.byref(v), ctypes.byref(c)))
+        return v.value, c.value
+
+    @property
+    def blocks(self):
+        return int(self._lib.tlbm_batch_blocks(self._h))

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/tlbm.h"
 #include "tlbm_internal.h"
@@ -473,6 +474,239 @@ tlbm_status tlbm_set_state(tlbm* t, const void* host, size_t bytes) {
     CK(cudaMemsetAsync(t->d.flag, 0, sizeof(int), t->st));
     CK(cudaStreamSynchronize(t->st));
     return TLBM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+
+struct tlbm_batch {
+    tlbm_host::BatchState bs;
+    std::vector<tlbm*> members;
+    std::vector<DevState*> sims;
+    std::vector<tlbm_host::PhysD> phys;  // members' parameters baked into the descriptors
+    const Ops* ops;
+    cudaStream_t st;       // the members' stream
+    cudaStream_t cap;      // private stream used only to capture the step graph
+    cudaGraphExec_t exec;  // two batched steps (parity returns to graph_par)
+    int graph_par;
+    int use_graph;
+    std::string err;
+};
+
+namespace {
+
+tlbm_status bfail(tlbm_batch* b, tlbm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_create_err = buf;
+    return s;
+}
+
+void drop_graph(tlbm_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+tlbm_status batch_rebuild(tlbm_batch* b) {
+    drop_graph(b);
+    cudaError_t e = b->ops->batch_build(b->bs, b->st);
+    if (e != cudaSuccess)
+        return bfail(b, e == cudaErrorInvalidConfiguration ? TLBM_ERR_ARG : TLBM_ERR_CUDA,
+                     "batch set-up failed: %s", cudaGetErrorString(e));
+    b->phys.clear();
+    for (DevState* d : b->sims) b->phys.push_back(d->phys);
+    return TLBM_OK;
+}
+
+// members at one buffer parity, with the parameters the descriptors hold
+// (rebuilt when tlbm_set_gamma changed a member since)
+tlbm_status batch_aligned(tlbm_batch* b) {
+    for (size_t k = 1; k < b->sims.size(); ++k)
+        if (b->sims[k]->cur != b->sims[0]->cur)
+            return bfail(b, TLBM_ERR_ARG, "batch members are at different step parities (a member was stepped alone)");
+    bool same = b->phys.size() == b->sims.size();
+    for (size_t k = 0; same && k < b->sims.size(); ++k)
+        same = memcmp(&b->phys[k], &b->sims[k]->phys, sizeof(tlbm_host::PhysD)) == 0;
+    return same ? TLBM_OK : batch_rebuild(b);
+}
+
+tlbm_status batch_plain_steps(tlbm_batch* b, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) {
+        cudaError_t e = b->ops->batch_step(b->bs, b->st);
+        if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "batched step: %s", cudaGetErrorString(e));
+        for (tlbm* m : b->members) ++m->steps;
+    }
+    return TLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tlbm_status tlbm_batch_create(tlbm_batch** out, tlbm* const* members, int count) {
+    g_create_err.clear();
+    if (!out || !members || count < 1) return bfail(nullptr, TLBM_ERR_ARG, "need at least one member");
+    *out = nullptr;
+    for (int k = 0; k < count; ++k) {
+        const tlbm* m = members[k];
+        if (!m) return bfail(nullptr, TLBM_ERR_ARG, "member %d is NULL", k);
+        const tlbm* m0 = members[0];
+        if (m->d.Q != m0->d.Q || m->d.prec != m0->d.prec)
+            return bfail(nullptr, TLBM_ERR_ARG, "members must share lattice and precision");
+        if (m->st != m0->st || m->device != m0->device)
+            return bfail(nullptr, TLBM_ERR_ARG, "members must share the device and stream");
+        if ((m->d.solid != nullptr) != (m0->d.solid != nullptr))
+            return bfail(nullptr, TLBM_ERR_ARG, "members must all have, or all lack, solid nodes");
+        for (int j = 0; j < k; ++j)
+            if (members[j] == m) return bfail(nullptr, TLBM_ERR_ARG, "member %d appears twice", k);
+    }
+    tlbm_batch* b = new tlbm_batch();
+    b->members.assign(members, members + count);
+    for (tlbm* m : b->members) b->sims.push_back(&m->d);
+    b->ops = members[0]->ops;
+    b->st = members[0]->st;
+    b->cap = nullptr;
+    b->exec = nullptr;
+    b->graph_par = 0;
+    b->use_graph = 0;
+    memset(&b->bs, 0, sizeof b->bs);
+    b->bs.count = count;
+    b->bs.sims = b->sims.data();
+    b->bs.tile = 0;
+    tlbm_status s = batch_aligned(b);  // first build: no parameters recorded yet
+    if (s != TLBM_OK) {
+        g_create_err = b->err;
+        tlbm_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return TLBM_OK;
+}
+
+void tlbm_batch_destroy(tlbm_batch* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    else cudaDeviceSynchronize();
+    drop_graph(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaFree(b->bs.desc);
+    delete b;
+}
+
+const char* tlbm_batch_last_error(const tlbm_batch* b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+int64_t tlbm_batch_blocks(const tlbm_batch* b) { return b ? (int64_t)b->bs.blocks : -1; }
+
+tlbm_status tlbm_batch_set_tile(tlbm_batch* b, int variant, int chunk) {
+    if (!b) return TLBM_ERR_ARG;
+    if (variant < 0 || variant > 255 || (variant & 15) > 3 || chunk < 0 || chunk > 4096)
+        return bfail(b, TLBM_ERR_ARG, "bad tile");
+    const int old = b->bs.tile;
+    b->bs.tile = variant + 256 * chunk;
+    tlbm_status s = batch_rebuild(b);
+    if (s != TLBM_OK) {  // keep the previous, working tile
+        b->bs.tile = old;
+        batch_rebuild(b);
+    }
+    return s;
+}
+
+tlbm_status tlbm_batch_set_graph(tlbm_batch* b, int on) {
+    if (!b) return TLBM_ERR_ARG;
+    b->use_graph = on ? 1 : 0;
+    if (!on) drop_graph(b);
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_batch_step(tlbm_batch* b, int64_t nsteps) {
+    if (!b) return TLBM_ERR_ARG;
+    if (nsteps < 0) return bfail(b, TLBM_ERR_ARG, "nsteps must be >= 0");
+    tlbm_status s = batch_aligned(b);
+    if (s != TLBM_OK) return s;
+    if (!b->use_graph || nsteps < 2) return batch_plain_steps(b, nsteps);
+    // graph of two batched steps, captured once on a private stream and replayed
+    // on the members' stream; it starts and ends at buffer parity graph_par
+    if (b->exec && b->sims[0]->cur != b->graph_par) {
+        s = batch_plain_steps(b, 1);
+        if (s != TLBM_OK) return s;
+        --nsteps;
+    }
+    if (!b->exec) {
+        cudaError_t e = cudaSuccess;
+        if (!b->cap) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        const int par = b->sims[0]->cur;
+        cudaError_t e1 = b->ops->batch_step(b->bs, b->cap);
+        cudaError_t e2 = b->ops->batch_step(b->bs, b->cap);  // parity is back to par
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(b->cap, &graph);
+        if (e == cudaSuccess && e1 == cudaSuccess && e2 == cudaSuccess)
+            e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e == cudaSuccess) e = (e1 != cudaSuccess) ? e1 : e2;
+        if (e != cudaSuccess) {
+            drop_graph(b);
+            return bfail(b, TLBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        b->graph_par = par;
+    }
+    for (int64_t k = 0; k + 1 < nsteps; k += 2) {
+        cudaError_t e = cudaGraphLaunch(b->exec, b->st);
+        if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+        for (tlbm* m : b->members) m->steps += 2;
+    }
+    return batch_plain_steps(b, nsteps & 1);
+}
+
+tlbm_status tlbm_batch_autotune(tlbm_batch* b, int trial_steps, int* variant, int* chunk) {
+    if (!b || trial_steps < 1) return TLBM_ERR_ARG;
+    tlbm_status s = batch_aligned(b);
+    if (s != TLBM_OK) return s;
+    const bool solid = b->sims[0]->solid != nullptr;
+    const bool d2 = b->sims[0]->Q == 9;
+    std::vector<int> shapes = {0};
+    if (solid && d2 && b->sims[0]->prec != 0) shapes = {1, 2, 3};
+    const int chunks[] = {0, 16, 32, 64};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return bfail(b, TLBM_ERR_CUDA, "cudaEventCreate failed");
+    }
+    float best = 3.0e38f;
+    int bv = 0, bc = 0;
+    const int old = b->bs.tile;
+    for (int sh : shapes) {
+        for (int ch : chunks) {
+            b->bs.tile = sh + 256 * ch;
+            if (batch_rebuild(b) != TLBM_OK) continue;  // e.g. too many blocks for the partial sums
+            if (batch_plain_steps(b, 1) != TLBM_OK) continue;
+            cudaEventRecord(e0, b->st);
+            if (batch_plain_steps(b, trial_steps) != TLBM_OK) continue;
+            cudaEventRecord(e1, b->st);
+            float ms = 0.0f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+            if (ms < best) {
+                best = ms;
+                bv = sh;
+                bc = ch;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->bs.tile = best < 3.0e38f ? bv + 256 * bc : old;
+    s = batch_rebuild(b);
+    if (s != TLBM_OK) return s;
+    if (variant) *variant = bv;
+    if (chunk) *chunk = bc;
+    return best < 3.0e38f ? TLBM_OK : bfail(b, TLBM_ERR_CUDA, "no tile candidate ran");
 }
 
 }  // extern "C"

@@ -25,6 +25,8 @@
 // write of the 3Q populations plus the halo's share (about 2/MC extra planes).
 #pragma once
 
+#include <vector>
+
 #include "tlbm_kernels.cuh"
 
 namespace tlbm_dev {
@@ -66,9 +68,9 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // HINT: 1 streams the stores out (evict-first); 2 also marks phase C's loads,
 //       the last use of those lines, evict-first.
 template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false, int HINT = 0>
-__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))  // 16 warps per SM
-k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename Store<S>::T> P,
-        double* __restrict__ partials) {
+__device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__ src, S* __restrict__ dst,
+                                           const Phys<typename Store<S>::T>& P, double* __restrict__ partials,
+                                           const int bid) {
     using T = typename Store<S>::T;
     using A = Axes<Q>;
     constexpr int D = Lat<Q>::D;
@@ -85,8 +87,8 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int tileA = blockIdx.x % g.tilesA;
-    const int rest = blockIdx.x / g.tilesA;
+    const int tileA = bid % g.tilesA;
+    const int rest = bid / g.tilesA;
     const int tileB = rest % g.tilesB;
     const int chunk = rest / g.tilesB;
     const int A0 = tileA * TX, B0 = tileB * TY;
@@ -343,10 +345,17 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
 
     block_sum3(mr, mp, ms);
     if (tid == 0) {
-        partials[3 * blockIdx.x + 0] = mr;
-        partials[3 * blockIdx.x + 1] = mp;
-        partials[3 * blockIdx.x + 2] = ms;
+        partials[3 * bid + 0] = mr;
+        partials[3 * bid + 1] = mp;
+        partials[3 * bid + 2] = ms;
     }
+}
+
+template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false, int HINT = 0>
+__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))  // 16 warps per SM
+k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename Store<S>::T> P,
+        double* __restrict__ partials) {
+    fused_body<Q, S, TX, TY, ILP, EARLY, PF, HINT>(g, src, dst, P, partials, blockIdx.x);
 }
 
 // ------------------------------------------------------ solid-aware variant
@@ -382,9 +391,10 @@ __global__ void k_nbmask(Geom g, const uint8_t* __restrict__ solid, uint32_t* __
 // The moment and mask rings have five plane slots and the momentum ring four, so
 // a fast warp writing plane m+2 never touches data a slow warp still reads.
 template <int Q, typename S, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
-k_fused_solid(MGeom g, const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ nbm,
-              Phys<typename Store<S>::T> P, double* __restrict__ partials) {
+__device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__ src, S* __restrict__ dst,
+                                           const uint32_t* __restrict__ nbm,
+                                           const Phys<typename Store<S>::T>& P, double* __restrict__ partials,
+                                           const int bid) {
     using T = typename Store<S>::T;
     using A = Axes<Q>;
     constexpr int D = Lat<Q>::D;
@@ -405,8 +415,8 @@ k_fused_solid(MGeom g, const S* __restrict__ src, S* __restrict__ dst, const uin
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int tileA = blockIdx.x % g.tilesA;
-    const int rest = blockIdx.x / g.tilesA;
+    const int tileA = bid % g.tilesA;
+    const int rest = bid / g.tilesA;
     const int tileB = rest % g.tilesB;
     const int chunk = rest / g.tilesB;
     const int A0 = tileA * TX, B0 = tileB * TY;
@@ -664,9 +674,89 @@ k_fused_solid(MGeom g, const S* __restrict__ src, S* __restrict__ dst, const uin
 
     block_sum3(mr, mp, ms);
     if (tid == 0) {
-        partials[3 * blockIdx.x + 0] = mr;
-        partials[3 * blockIdx.x + 1] = mp;
-        partials[3 * blockIdx.x + 2] = ms;
+        partials[3 * bid + 0] = mr;
+        partials[3 * bid + 1] = mp;
+        partials[3 * bid + 2] = ms;
+    }
+}
+
+template <int Q, typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
+k_fused_solid(MGeom g, const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ nbm,
+              Phys<typename Store<S>::T> P, double* __restrict__ partials) {
+    solid_body<Q, S, TX, TY>(g, src, dst, nbm, P, partials, blockIdx.x);
+}
+
+// ------------------------------------------------------------- batches
+
+// One member of a batched step: its geometry, buffers for this step's parity,
+// neighbour mask (solid lattices), physics, partial sums and first block.
+template <typename T>
+struct SimDesc {
+    MGeom g;
+    const void* src;
+    void* dst;
+    const uint32_t* nbm;
+    Phys<T> P;
+    double* partials;
+    double* step_mass;
+    int* flag;
+    int block0;  // first block of this member in the batched grid
+    int nblocks;
+};
+
+// block -> member: the last descriptor whose block0 <= blockIdx.x; the member's
+// descriptor is copied to shared memory for the body to read
+template <typename T>
+__device__ __forceinline__ const SimDesc<T>& batch_member(const SimDesc<T>* __restrict__ d, int nsims,
+                                                          SimDesc<T>& sh) {
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nsims - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (d[mid].block0 <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        sh = d[lo];
+    }
+    __syncthreads();
+    return sh;
+}
+
+template <int Q, typename S, int TX, int TY, bool PF, int HINT>
+__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
+k_fused_batch(const SimDesc<typename Store<S>::T>* __restrict__ d, int nsims) {
+    __shared__ SimDesc<typename Store<S>::T> sh;
+    const SimDesc<typename Store<S>::T>& m = batch_member(d, nsims, sh);
+    fused_body<Q, S, TX, TY, false, false, PF, HINT>(m.g, static_cast<const S*>(m.src), static_cast<S*>(m.dst),
+                                                     m.P, m.partials, (int)blockIdx.x - m.block0);
+}
+
+template <int Q, typename S, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
+k_fused_solid_batch(const SimDesc<typename Store<S>::T>* __restrict__ d, int nsims) {
+    __shared__ SimDesc<typename Store<S>::T> sh;
+    const SimDesc<typename Store<S>::T>& m = batch_member(d, nsims, sh);
+    solid_body<Q, S, TX, TY>(m.g, static_cast<const S*>(m.src), static_cast<S*>(m.dst), m.nbm, m.P,
+                             m.partials, (int)blockIdx.x - m.block0);
+}
+
+// FP64 totals of every member: block i sums member i's partials in a fixed order
+template <typename T>
+__global__ void k_mass_final_batch(const SimDesc<T>* __restrict__ d) {
+    const SimDesc<T>& m = d[blockIdx.x];
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = threadIdx.x; k < m.nblocks; k += blockDim.x) {
+        a += m.partials[3 * k];
+        b += m.partials[3 * k + 1];
+        c += m.partials[3 * k + 2];
+    }
+    block_sum3(a, b, c);
+    if (threadIdx.x == 0) {
+        m.step_mass[0] = a;
+        m.step_mass[1] = b;
+        m.step_mass[2] = c;
+        if (!(isfinite(a) && isfinite(b) && isfinite(c))) *m.flag = 1;
     }
 }
 
@@ -697,7 +787,7 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
     if (d.solid) {
         // solid-aware kernel: a fixed tile per lattice (D3Q19 in double: 16x4 keeps
         // its five-plane rings under the 48 KB static shared-memory limit)
-        c.TX = Q == 19 ? (dbl ? 16 : 32) : 128;
+        c.TX = Q == 19 ? (dbl ? 16 : 32) : (dbl ? 128 : (variant == 2 ? 256 : (variant == 3 ? 64 : 128)));
         c.TY = Q == 19 ? 4 : 1;
     } else if (Q == 19 && dbl) {
         c.TX = 16;  // double storage: a smaller tile keeps the static shared ring small
@@ -788,7 +878,9 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
             if constexpr (sizeof(S) == 8) gos(k_fused_solid<Q, S, 16, 4>, 64);
             else gos(k_fused_solid<Q, S, 32, 4>, 128);
         } else {
-            gos(k_fused_solid<Q, S, 128, 1>, 128);
+            if (c.TX == 256) gos(k_fused_solid<Q, S, 256, 1>, 256);
+            else if (c.TX == 64) gos(k_fused_solid<Q, S, 64, 1>, 64);
+            else gos(k_fused_solid<Q, S, 128, 1>, 128);
         }
         return cudaGetLastError();
     }
@@ -840,6 +932,93 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
             go(k_fused<Q, S, 128, 1, false, false>, 128);  // plain loop
         }
     }
+    return cudaGetLastError();
+}
+
+// ---- batches: every member uses the batch's tile; descriptors for both parities
+
+template <int Q, typename S>
+inline cudaError_t batch_build(tlbm_host::BatchState& b, cudaStream_t st) {
+    using T = typename Store<S>::T;
+    const int n = b.count;
+    if (n < 1) return cudaErrorInvalidValue;
+    const bool solid = b.sims[0]->solid != nullptr;
+    std::vector<SimDesc<T>> h(2 * (size_t)n);
+    long long block0 = 0;
+    for (int k = 0; k < n; ++k) {
+        tlbm_host::DevState& d = *b.sims[k];
+        if ((d.solid != nullptr) != solid || d.cur != b.sims[0]->cur) return cudaErrorInvalidValue;
+        if (solid && !d.nbm_ready) {
+            const Geom gg{d.nx, d.ny, d.nz, d.N, d.Np, d.ncx};
+            k_nbmask<Q><<<1216, 256, 0, st>>>(gg, d.solid, d.nbm);
+            d.nbm_ready = 1;
+        }
+        tlbm_host::DevState dd = d;
+        dd.tile = b.tile;
+        const FusedCfg<Q> c = fused_cfg<Q>(dd);
+        // shapes with a batched kernel (batch_step): every solid shape; periodic
+        // D3Q19 32x4 (16x8 in double), periodic D2Q9 128
+        const bool shape_ok = solid || (Q == 19 ? (sizeof(S) == 8 ? (c.TX == 16 && c.TY == 8) : (c.TX == 32 && c.TY == 4))
+                                                : c.TX == 128);
+        if (!shape_ok) return cudaErrorInvalidConfiguration;
+        const MGeom g = mgeom<Q, S>(dd, c);
+        const long long nb = (long long)g.tilesA * g.tilesB * ((g.NM + g.MC - 1) / g.MC);
+        if (nb > d.partials_cap) return cudaErrorInvalidConfiguration;
+        for (int par = 0; par < 2; ++par) {
+            SimDesc<T>& e = h[(size_t)par * n + k];
+            e.g = g;
+            e.src = d.pop[par];
+            e.dst = d.pop[1 - par];
+            e.nbm = d.nbm;
+            e.P = to_phys<T>(d.phys);
+            e.partials = d.partials;
+            e.step_mass = d.step_mass;
+            e.flag = d.flag;
+            e.block0 = (int)block0;
+            e.nblocks = (int)nb;
+        }
+        block0 += nb;
+    }
+    if (block0 > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    b.blocks = block0;
+    cudaError_t e = cudaSuccess;
+    if (!b.desc) e = cudaMalloc(&b.desc, sizeof(SimDesc<T>) * 2 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.desc, h.data(), sizeof(SimDesc<T>) * 2 * (size_t)n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) b.built = 1;
+    return e;
+}
+
+template <int Q, typename S>
+inline cudaError_t batch_step(tlbm_host::BatchState& b, cudaStream_t st) {
+    using T = typename Store<S>::T;
+    const int n = b.count;
+    const int par = b.sims[0]->cur;
+    const SimDesc<T>* d = static_cast<const SimDesc<T>*>(b.desc) + (size_t)par * n;
+    tlbm_host::DevState probe = *b.sims[0];
+    probe.tile = b.tile;
+    const FusedCfg<Q> c = fused_cfg<Q>(probe);
+    const int nb = (int)b.blocks;
+    if (probe.solid) {
+        if constexpr (Q == 19) {
+            if constexpr (sizeof(S) == 8) k_fused_solid_batch<Q, S, 16, 4><<<nb, 64, 0, st>>>(d, n);
+            else k_fused_solid_batch<Q, S, 32, 4><<<nb, 128, 0, st>>>(d, n);
+        } else {
+            if (c.TX == 256) k_fused_solid_batch<Q, S, 256, 1><<<nb, 256, 0, st>>>(d, n);
+            else if (c.TX == 64) k_fused_solid_batch<Q, S, 64, 1><<<nb, 64, 0, st>>>(d, n);
+            else k_fused_solid_batch<Q, S, 128, 1><<<nb, 128, 0, st>>>(d, n);
+        }
+    } else {
+        if constexpr (Q == 19) {
+            if constexpr (sizeof(S) == 8) k_fused_batch<Q, S, 16, 8, false, 0><<<nb, 128, 0, st>>>(d, n);
+            else if constexpr (sizeof(S) == 2) k_fused_batch<Q, S, 32, 4, true, 1><<<nb, 128, 0, st>>>(d, n);
+            else k_fused_batch<Q, S, 32, 4, false, 1><<<nb, 128, 0, st>>>(d, n);
+        } else {
+            k_fused_batch<Q, S, 128, 1, true, 2><<<nb, 128, 0, st>>>(d, n);
+        }
+    }
+    k_mass_final_batch<T><<<n, kThreads, 0, st>>>(d);
+    for (int k = 0; k < n; ++k) b.sims[k]->cur ^= 1;
     return cudaGetLastError();
 }
 

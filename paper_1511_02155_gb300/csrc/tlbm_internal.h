@@ -41,6 +41,17 @@ struct DevState {
     long long partials_cap;  // blocks whose partial sums fit in the first part of partials
 };
 
+// A batch of engines of one lattice and storage format, advanced together by
+// one launch per step.
+struct BatchState {
+    int count;
+    DevState** sims;     // member engines' device states
+    void* desc;          // device descriptor array: [2][count], one set per buffer parity
+    int tile;            // tile choice for every member (DevState::tile encoding)
+    long long blocks;    // blocks of one batched step
+    int built;           // descriptors are current
+};
+
 struct Ops {
     // one time step; flips cur.  When ev0/ev1 are not null they are recorded on
     // the stream just before and just after the step's main kernel(s).
@@ -56,6 +67,10 @@ struct Ops {
     cudaError_t (*set_pops)(DevState& d, const double* in, cudaStream_t st);
     int (*launches)(const DevState& d, int kind);
     bool (*has_fused)(const DevState& d);
+    // batches: build the descriptors of both parities (and neighbour masks);
+    // one step of every member (flips every member's cur)
+    cudaError_t (*batch_build)(BatchState& b, cudaStream_t st);
+    cudaError_t (*batch_step)(BatchState& b, cudaStream_t st);
 };
 
 // one table per storage format; nullptr if the lattice is not built

@@ -20,6 +20,23 @@
 namespace tlbm_dev {
 
 constexpr int kThreads = 256;
+
+// physical parameters in the compute type
+template <typename T>
+inline Phys<T> to_phys(const tlbm_host::PhysD& p) {
+    Phys<T> q;
+    for (int m = 0; m < 3; ++m) {
+        q.kappa[m] = T(p.kappa[m]);
+        q.omega[m] = T(p.omega[m]);
+        q.Gw[m] = T(p.Gw[m]);
+        for (int n = 0; n < 3; ++n) q.K[m][n] = T(p.K[m][n]);
+    }
+    q.a2 = T(p.a2);
+    q.gamma[0] = T(p.gamma[0]);
+    q.gamma[1] = T(p.gamma[1]);
+    return q;
+}
+
 constexpr int kMassBlocks = 1216;  // 8 x 152 SMs; fixed so reductions are repeatable
 
 // ------------------------------------------------------------ small helpers

@@ -10,21 +10,6 @@ namespace tlbm_dev {
 using tlbm_host::DevState;
 using tlbm_host::PhysD;
 
-template <typename T>
-inline Phys<T> to_phys(const PhysD& p) {
-    Phys<T> q;
-    for (int m = 0; m < 3; ++m) {
-        q.kappa[m] = T(p.kappa[m]);
-        q.omega[m] = T(p.omega[m]);
-        q.Gw[m] = T(p.Gw[m]);
-        for (int n = 0; n < 3; ++n) q.K[m][n] = T(p.K[m][n]);
-    }
-    q.a2 = T(p.a2);
-    q.gamma[0] = T(p.gamma[0]);
-    q.gamma[1] = T(p.gamma[1]);
-    return q;
-}
-
 inline Geom geom(const DevState& d) { return Geom{d.nx, d.ny, d.nz, d.N, d.Np, d.ncx}; }
 
 inline int grid_for(long long n) {
@@ -133,9 +118,12 @@ struct Impl {
 
     static bool has_fused(const DevState& d) { return fused_supported<Q, S>(d); }
 
+    static cudaError_t bbuild(tlbm_host::BatchState& b, cudaStream_t st) { return batch_build<Q, S>(b, st); }
+    static cudaError_t bstep(tlbm_host::BatchState& b, cudaStream_t st) { return batch_step<Q, S>(b, st); }
+
     static const tlbm_host::Ops* table() {
-        static const tlbm_host::Ops o = {&step, &init, &fields, &mass, &get_box, &set_pops, &launches,
-                                         &has_fused};
+        static const tlbm_host::Ops o = {&step,     &init,      &fields, &mass,  &get_box, &set_pops,
+                                         &launches, &has_fused, &bbuild, &bstep};
         return &o;
     }
 };
