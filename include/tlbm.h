@@ -243,6 +243,33 @@ tlbm_status tlbm_step_noalloc(tlbm_lattice lattice, tlbm_precision precision, in
                               double M_psi, const double h[3], const uint8_t *solid_dev,
                               const void *src_dev, void *dst_dev, double *mass_dev, void *cuda_stream);
 
+/* ------------------------------------------------------------------ wetting theory
+ * Host-only functions (no GPU involved) of the model's wetting theory,
+ * Sec. Surface Thermodynamics and Sec. Inverting the contact angle relations.
+ * Solid-fluid tensions gamma_sm = I_m + sum_{n != m} J_n (Eq. solidST), fluid-fluid
+ * tensions gamma_mn = alpha (kappa_m + kappa_n)/6 (Eq. SurfTens), angles from
+ * Young's equation (Eq. contact angle): cos theta_mn = (gamma_sn - gamma_sm)/gamma_mn,
+ * theta_mn measured through fluid m.  The closed form used,
+ *   cos theta_mn = (D_m - D_n) / (2 alpha (kappa_m + kappa_n)),
+ *   D_j = [(alpha kappa_j + 4 h_j)^{3/2} - (alpha kappa_j - 4 h_j)^{3/2}] / sqrt(alpha kappa_j),
+ * is what I_m, J_n and Young's equation give; the printed Eq. invertCA has the
+ * opposite sign and no 1/alpha.
+ */
+
+/* theta_deg[0..2] = theta_12, theta_23, theta_31 in degrees for wetting parameters
+ * h[0..2].  TLBM_ERR_ARG for NULL pointers or kappa_m, alpha not > 0;
+ * TLBM_ERR_PARAM unless |4 h_m| < alpha kappa_m for every m. */
+tlbm_status tlbm_contact_angles(const double kappa[3], double alpha, const double h[3], double theta_deg[3]);
+
+/* Wetting parameters h[0..2] that give the contact angles theta_12 and theta_13
+ * (both measured through fluid 1, degrees, in (0, 180)), with the gauge
+ * sum_m h_m / kappa_m = 0 (Eq. Redundancy: zero wall-normal gradient of rho).
+ * theta_23 then follows from the Girifalco-Good relation.  TLBM_ERR_PARAM when no
+ * admissible h exists (theta_23 would not exist, or some |4 h_m| would reach
+ * alpha kappa_m); h is written only on success. */
+tlbm_status tlbm_wetting_from_angles(const double kappa[3], double alpha, double theta12_deg,
+                                     double theta13_deg, double h[3]);
+
 /* ------------------------------------------------------------------ batches
  * Many independent lattices of one lattice type and storage format (for example
  * a contact-angle or kappa sweep over lattices of uneven size) advanced by ONE

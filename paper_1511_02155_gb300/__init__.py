@@ -20,7 +20,7 @@ import threading
 
 import numpy as np
 
-__all__ = ["TernaryLB", "TernaryBatch", "TLBMError", "load_library", "lib_path", "D2Q9", "D3Q19",
+__all__ = ["TernaryLB", "TernaryBatch", "TLBMError", "contact_angles", "wetting_from_angles", "load_library", "lib_path", "D2Q9", "D3Q19",
            "FP64", "FP32", "FP16_OFFSET", "BF16_OFFSET", "KERNEL_AUTO", "KERNEL_FUSED",
            "KERNEL_SPLIT"]
 
@@ -90,6 +90,8 @@ def _declare(lib):
         "tlbm_batch_blocks": (i64, [_H]),
         "tlbm_batch_last_error": (ctypes.c_char_p, [_H]),
         "tlbm_batch_destroy": (None, [_H]),
+        "tlbm_contact_angles": (i, [_dp, d, _dp, _dp]),
+        "tlbm_wetting_from_angles": (i, [_dp, d, d, d, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -294,6 +296,30 @@ class TernaryLB:
     def set_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         self._check(self._lib.tlbm_set_state(self._h, buf.ctypes.data_as(_vp), buf.size))
+
+
+def contact_angles(kappa, alpha, h):
+    """(theta_12, theta_23, theta_31) in degrees for wetting parameters h (host code)."""
+    lib = load_library()
+    k, kp = _arr(kappa, 3)
+    hh, hp = _arr(h, 3)
+    out = np.zeros(3)
+    rc = lib.tlbm_contact_angles(kp, float(alpha), hp, out.ctypes.data_as(_dp))
+    if rc != 0:
+        raise TLBMError(rc, "no contact angles for these parameters")
+    return tuple(float(v) for v in out)
+
+
+def wetting_from_angles(kappa, alpha, theta12, theta13):
+    """Wetting parameters (h_1, h_2, h_3) giving theta_12 and theta_13 (through fluid 1,
+    degrees) with the gauge sum h_m/kappa_m = 0 (host code)."""
+    lib = load_library()
+    k, kp = _arr(kappa, 3)
+    out = np.zeros(3)
+    rc = lib.tlbm_wetting_from_angles(kp, float(alpha), float(theta12), float(theta13), out.ctypes.data_as(_dp))
+    if rc != 0:
+        raise TLBMError(rc, f"no admissible wetting parameters for theta_12={theta12}, theta_13={theta13}")
+    return tuple(float(v) for v in out)
 
 
 class TernaryBatch:

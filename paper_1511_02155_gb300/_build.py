@@ -27,6 +27,7 @@ UNITS = {
     "tlbm_f16.cu": [],
     "tlbm_bf16.cu": [],
     "tlbm_noalloc.cu": ["-fmad=false"],
+    "tlbm_wetting.cpp": [],
 }
 
 
@@ -64,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     procs = []
     objs = []
     for unit, flags in UNITS.items():
-        obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(unit)[0] + ".o")
         objs.append(obj)
         cmd = [cc, "-c", os.path.join(CSRC, unit), "-o", obj, *common, *flags]
         procs.append((unit, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
