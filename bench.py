@@ -46,6 +46,10 @@ def bytes_per_node(Q: int, precision: str) -> int:
     return 2 * 3 * Q * {"fp64": 8, "fp32": 4}[precision]
 
 
+SWEEP_LABEL = ("96 D2Q9 square-well contact-angle runs of uneven size (128x64 .. 768x384), "
+               "target angles in [30, 150] deg, batched (one launch per step) under a CUDA graph")
+
+
 def workload(name: str, size: int = 0):
     """(config dict, label).  size overrides the edge of the spinodal / probe
     lattices (used for small profiling cases of the same kernel)."""
@@ -177,10 +181,14 @@ def cpu_baseline(cfg_name: str, cfg: dict, budget_s: float = 12.0):
         elif cfg_name == "wells4096":
             wc = W.wells_2d(nx, ny, 2)
             C, solid = wc["C"], wc["solid"]
+        elif cfg_name == "sweep96":
+            C, solid = W.square_well(nx, ny // 2, 70, 35, floor=8)
+            ny = ny // 2
         else:
             C = W.spinodal((ny, nx), seed=5)
         shape = (nx, ny, 1)
-        sample = f"D2Q9 {nx}x{ny} sub-lattice of the same recipe"
+        sample = (f"D2Q9 {nx}x{ny} square well of the same recipe (one member-sized lattice)"
+                  if cfg_name == "sweep96" else f"D2Q9 {nx}x{ny} sub-lattice of the same recipe")
     p = oracle.make_params(Q, *shape, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"], cfg["M_psi"],
                            cfg.get("h", (0.0, 0.0, 0.0)))
     rho, phi, psi = W.to_aux(*C)
@@ -240,6 +248,156 @@ def run_reference(args, cfg_name, cfg, label):
     print(json.dumps(line), flush=True)
 
 
+def sweep_members(precision: str, count: int = 96):
+    """Engines of the contact-angle sweep, h from each member's first admissible
+    target pair (the library's wetting inversion)."""
+    import paper_1511_02155_gb300 as tl
+    members = W.sweep_wells(count)
+    engines, hosts = [], []
+    for m in members:
+        for a in m["angles"]:
+            try:
+                m["h"] = tl.wetting_from_angles(m["kappa"], m["alpha"], *a)
+                m["target"] = a
+                break
+            except tl.TLBMError:
+                continue
+        rho, phi, psi = W.to_aux(*m["C"])
+        m["C"] = None
+        for a in (rho, phi, psi):
+            a[m["solid"] != 0] = 0.0
+        eng = tl.TernaryLB(9, m["nx"], m["ny"], 1, m["kappa"], m["alpha"], m["tau_f"], m["M_phi"],
+                           m["M_psi"], m["h"], m["solid"], precision)
+        eng.init_fields(rho, phi, psi)
+        engines.append(eng)
+        hosts.append((rho, phi, psi))
+    return members, engines, hosts
+
+
+def run_sweep(args):
+    """Batched contact-angle sweep: every member advanced by one launch per step."""
+    import torch
+    import paper_1511_02155_gb300 as tl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    members, engines, hosts = sweep_members(args.precision)
+    N = sum(m["nx"] * m["ny"] for m in members)
+    n_fluid = sum(int(m["nx"] * m["ny"] - np.count_nonzero(m["solid"])) for m in members)
+    batch = tl.TernaryBatch(engines)
+    tile = batch.autotune(trial_steps=5)  # real steps: part of the warm-up
+    batch.set_graph(True)
+    batch.step(args.warmup)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        e0.record(stream)
+        batch.step(args.steps)
+        e1.record(stream)
+        barrier()
+    ms = reduce_max(e0.elapsed_time(e1), dist)
+    clocks = clk.summary()
+    for e in engines:
+        e.step_mass()  # raises on a non-finite total
+    value = job_mlups(world, N, args.steps, ms / 1e3)
+
+    # the same members stepped one by one (two launches each per step), for comparison
+    ks = max(3, min(args.steps, 20))
+    barrier()
+    e0.record(stream)
+    for _ in range(ks):
+        for e in engines:
+            e.step(1)
+    e1.record(stream)
+    barrier()
+    lone_mlups = job_mlups(world, N, ks, reduce_max(e0.elapsed_time(e1), dist) / 1e3)
+
+    # main-kernel duration (CUDA events on the members' stream around each batched launch)
+    batch.set_timing(True)
+    batch.step(min(args.steps, 50))
+    kms, ksteps = batch.kernel_time()
+    batch.set_timing(False)
+    kernel_ms = kms / max(ksteps, 1)
+    bpn = bytes_per_node(9, args.precision)
+    alg_bytes = bpn * n_fluid + N
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    tag = f"batch:sweep96:{args.precision}:{tile[0]},{tile[1]}"
+    traffic = traffic_from_profiles(tag, kernel_source_digest(), N)
+
+    # end to end: upload every member's fields from pinned host memory, K batched
+    # steps, download C_1..3 of every member and their mass totals
+    pin = [[torch.from_numpy(np.ascontiguousarray(a.reshape(-1))).pin_memory() for a in h] for h in hosts]
+    outs = [[torch.empty(m["nx"] * m["ny"], dtype=torch.float64).pin_memory() for _ in range(3)]
+            for m in members]
+    barrier()
+    t0 = time.perf_counter()
+    for e, p in zip(engines, pin):
+        e.init_from_host_ptrs(*(t.data_ptr() for t in p))
+    batch.step(args.steps)
+    for e, o in zip(engines, outs):
+        e.fields_into(*(t.data_ptr() for t in o))
+        _ = e.mass()
+    barrier()
+    e2e_s = reduce_max(time.perf_counter() - t0, dist)
+    e2e = {"value": round(job_mlups(world, N, args.steps, e2e_s), 2), "unit": "MLUPS",
+           "h2d_bytes_per_step": round(3 * 8 * N / args.steps, 1),
+           "d2h_bytes_per_step": round((3 * 8 * N + 24 * len(members)) / args.steps, 1),
+           "job": f"upload rho/phi/psi of 96 members (fp64, pinned) + equilibrium init, {args.steps} "
+                  "batched steps, download C1..C3 (fp64) + mass totals of every member"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-store/f32",
+                                           "bf16": "bf16-store/f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": SWEEP_LABEL, "members": len(members), "nodes_per_gpu": N,
+                       "fluid_nodes_per_gpu": n_fluid, "lattice": "D2Q9", "precision": args.precision,
+                       "kernel": "batched fused (solid-aware)", "tile": list(tile),
+                       "blocks_per_launch": batch.blocks,
+                       "lone_engines_mlups": round(lone_mlups, 2),
+                       "l2": "populations exceed L2 (no flush needed)", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                         "kernel_ms": round(kernel_ms, 4),
+                         "algorithmic_bytes_per_launch": alg_bytes, "bytes_per_node": bpn},
+            "e2e": e2e,
+            "gpu_launches": args.steps * 2,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline("sweep96", {"Q": 9, "kappa": (0.01, 0.01, 0.01), "alpha": 1.0,
+                                                             "tau_f": 1.0, "M_phi": 0.5, "M_psi": 1.0 / 6.0})
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for e in engines:
+        e.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def reduce_max(value: float, dist, device="cuda") -> float:
     """Maximum of a per-rank scalar over all ranks (identity without a process group)."""
     if dist is None:
@@ -261,7 +419,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="spinodal256", choices=["spinodal256", "lens512", "probe8192", "wells4096"])
+    ap.add_argument("--workload", default="spinodal256",
+                    choices=["spinodal256", "lens512", "probe8192", "wells4096", "sweep96"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "split"])
     ap.add_argument("--tile", default="0,0")
@@ -270,6 +429,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.workload == "sweep96":
+        run_sweep(args)
+        return
     cfg, label = workload(args.workload, args.size)
 
     if args.impl == "reference":

@@ -303,6 +303,14 @@ tlbm_status tlbm_batch_autotune(tlbm_batch *b, int trial_steps, int *variant, in
  * a private stream at the next tlbm_batch_step, launched on the members' stream). */
 tlbm_status tlbm_batch_set_graph(tlbm_batch *b, int on);
 
+/* on != 0: record CUDA events around each batched step's main kernel and add
+ * its duration up (steps then run one by one, without the graph; the autotuner's
+ * trial steps are timed too).  Turning it on or off resets the sums. */
+tlbm_status tlbm_batch_set_timing(tlbm_batch *b, int on);
+
+/* Summed main-kernel time (ms) and the number of timed batched steps. */
+tlbm_status tlbm_batch_kernel_time(const tlbm_batch *b, double *ms_total, int64_t *steps);
+
 /* Blocks of one batched step launch. */
 int64_t tlbm_batch_blocks(const tlbm_batch *b);
 

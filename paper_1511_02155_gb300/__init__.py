@@ -88,6 +88,8 @@ def _declare(lib):
         "tlbm_batch_autotune": (i, [_H, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "tlbm_batch_set_graph": (i, [_H, i]),
         "tlbm_batch_blocks": (i64, [_H]),
+        "tlbm_batch_set_timing": (i, [_H, i]),
+        "tlbm_batch_kernel_time": (i, [_H, _dp, ctypes.POINTER(ctypes.c_int64)]),
         "tlbm_batch_last_error": (ctypes.c_char_p, [_H]),
         "tlbm_batch_destroy": (None, [_H]),
         "tlbm_contact_angles": (i, [_dp, d, _dp, _dp]),
@@ -379,3 +381,13 @@ class TernaryBatch:
     @property
     def blocks(self):
         return int(self._lib.tlbm_batch_blocks(self._h))
+
+    def set_timing(self, on=True):
+        self._check(self._lib.tlbm_batch_set_timing(self._h, 1 if on else 0))
+
+    def kernel_time(self):
+        """(total main-kernel ms, timed steps) since timing was turned on."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self._lib.tlbm_batch_kernel_time(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value

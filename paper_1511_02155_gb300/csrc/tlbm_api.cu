@@ -491,6 +491,10 @@ struct tlbm_batch {
     cudaGraphExec_t exec;  // two batched steps (parity returns to graph_par)
     int graph_par;
     int use_graph;
+    cudaEvent_t ev[2];     // main-kernel timing (tlbm_batch_set_timing)
+    int timing;
+    double kernel_ms;
+    int64_t kernel_steps;
     std::string err;
 };
 
@@ -537,7 +541,15 @@ tlbm_status batch_aligned(tlbm_batch* b) {
 
 tlbm_status batch_plain_steps(tlbm_batch* b, int64_t n) {
     for (int64_t k = 0; k < n; ++k) {
-        cudaError_t e = b->ops->batch_step(b->bs, b->st);
+        cudaError_t e = b->timing ? b->ops->batch_step(b->bs, b->st, b->ev[0], b->ev[1])
+                                  : b->ops->batch_step(b->bs, b->st, nullptr, nullptr);
+        if (e == cudaSuccess && b->timing) {
+            float ms = 0.0f;
+            e = cudaEventSynchronize(b->ev[1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+            b->kernel_ms += ms;
+            ++b->kernel_steps;
+        }
         if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "batched step: %s", cudaGetErrorString(e));
         for (tlbm* m : b->members) ++m->steps;
     }
@@ -574,6 +586,10 @@ tlbm_status tlbm_batch_create(tlbm_batch** out, tlbm* const* members, int count)
     b->exec = nullptr;
     b->graph_par = 0;
     b->use_graph = 0;
+    b->ev[0] = b->ev[1] = nullptr;
+    b->timing = 0;
+    b->kernel_ms = 0.0;
+    b->kernel_steps = 0;
     memset(&b->bs, 0, sizeof b->bs);
     b->bs.count = count;
     b->bs.sims = b->sims.data();
@@ -594,6 +610,8 @@ void tlbm_batch_destroy(tlbm_batch* b) {
     else cudaDeviceSynchronize();
     drop_graph(b);
     if (b->cap) cudaStreamDestroy(b->cap);
+    for (cudaEvent_t e : b->ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(b->bs.desc);
     delete b;
 }
@@ -623,12 +641,31 @@ tlbm_status tlbm_batch_set_graph(tlbm_batch* b, int on) {
     return TLBM_OK;
 }
 
+tlbm_status tlbm_batch_set_timing(tlbm_batch* b, int on) {
+    if (!b) return TLBM_ERR_ARG;
+    if (on && !b->ev[0]) {
+        if (cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess)
+            return bfail(b, TLBM_ERR_CUDA, "cudaEventCreate failed");
+    }
+    b->timing = on ? 1 : 0;
+    b->kernel_ms = 0.0;
+    b->kernel_steps = 0;
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_batch_kernel_time(const tlbm_batch* b, double* ms_total, int64_t* steps) {
+    if (!b || !ms_total || !steps) return TLBM_ERR_ARG;
+    *ms_total = b->kernel_ms;
+    *steps = b->kernel_steps;
+    return TLBM_OK;
+}
+
 tlbm_status tlbm_batch_step(tlbm_batch* b, int64_t nsteps) {
     if (!b) return TLBM_ERR_ARG;
     if (nsteps < 0) return bfail(b, TLBM_ERR_ARG, "nsteps must be >= 0");
     tlbm_status s = batch_aligned(b);
     if (s != TLBM_OK) return s;
-    if (!b->use_graph || nsteps < 2) return batch_plain_steps(b, nsteps);
+    if (!b->use_graph || b->timing || nsteps < 2) return batch_plain_steps(b, nsteps);
     // graph of two batched steps, captured once on a private stream and replayed
     // on the members' stream; it starts and ends at buffer parity graph_par
     if (b->exec && b->sims[0]->cur != b->graph_par) {
@@ -643,8 +680,8 @@ tlbm_status tlbm_batch_step(tlbm_batch* b, int64_t nsteps) {
         if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return bfail(b, TLBM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
         const int par = b->sims[0]->cur;
-        cudaError_t e1 = b->ops->batch_step(b->bs, b->cap);
-        cudaError_t e2 = b->ops->batch_step(b->bs, b->cap);  // parity is back to par
+        cudaError_t e1 = b->ops->batch_step(b->bs, b->cap, nullptr, nullptr);
+        cudaError_t e2 = b->ops->batch_step(b->bs, b->cap, nullptr, nullptr);  // parity is back to par
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(b->cap, &graph);
         if (e == cudaSuccess && e1 == cudaSuccess && e2 == cudaSuccess)

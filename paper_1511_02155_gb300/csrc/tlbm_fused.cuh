@@ -990,7 +990,8 @@ inline cudaError_t batch_build(tlbm_host::BatchState& b, cudaStream_t st) {
 }
 
 template <int Q, typename S>
-inline cudaError_t batch_step(tlbm_host::BatchState& b, cudaStream_t st) {
+inline cudaError_t batch_step(tlbm_host::BatchState& b, cudaStream_t st, cudaEvent_t ev0 = nullptr,
+                              cudaEvent_t ev1 = nullptr) {
     using T = typename Store<S>::T;
     const int n = b.count;
     const int par = b.sims[0]->cur;
@@ -999,6 +1000,7 @@ inline cudaError_t batch_step(tlbm_host::BatchState& b, cudaStream_t st) {
     probe.tile = b.tile;
     const FusedCfg<Q> c = fused_cfg<Q>(probe);
     const int nb = (int)b.blocks;
+    if (ev0) cudaEventRecord(ev0, st);
     if (probe.solid) {
         if constexpr (Q == 19) {
             if constexpr (sizeof(S) == 8) k_fused_solid_batch<Q, S, 16, 4><<<nb, 64, 0, st>>>(d, n);
@@ -1017,6 +1019,7 @@ inline cudaError_t batch_step(tlbm_host::BatchState& b, cudaStream_t st) {
             k_fused_batch<Q, S, 128, 1, true, 2><<<nb, 128, 0, st>>>(d, n);
         }
     }
+    if (ev1) cudaEventRecord(ev1, st);
     k_mass_final_batch<T><<<n, kThreads, 0, st>>>(d);
     for (int k = 0; k < n; ++k) b.sims[k]->cur ^= 1;
     return cudaGetLastError();

@@ -70,7 +70,8 @@ struct Ops {
     // batches: build the descriptors of both parities (and neighbour masks);
     // one step of every member (flips every member's cur)
     cudaError_t (*batch_build)(BatchState& b, cudaStream_t st);
-    cudaError_t (*batch_step)(BatchState& b, cudaStream_t st);
+    // one batched step of every member; ev0/ev1 (if not null) bracket the main kernel
+    cudaError_t (*batch_step)(BatchState& b, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
 };
 
 // one table per storage format; nullptr if the lattice is not built

@@ -119,7 +119,9 @@ struct Impl {
     static bool has_fused(const DevState& d) { return fused_supported<Q, S>(d); }
 
     static cudaError_t bbuild(tlbm_host::BatchState& b, cudaStream_t st) { return batch_build<Q, S>(b, st); }
-    static cudaError_t bstep(tlbm_host::BatchState& b, cudaStream_t st) { return batch_step<Q, S>(b, st); }
+    static cudaError_t bstep(tlbm_host::BatchState& b, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+        return batch_step<Q, S>(b, st, ev0, ev1);
+    }
 
     static const tlbm_host::Ops* table() {
         static const tlbm_host::Ops o = {&step,     &init,      &fields, &mass,  &get_box, &set_pops,

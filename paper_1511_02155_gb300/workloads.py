@@ -155,12 +155,14 @@ def walls_y(nx: int, ny: int, bottom: int = 1, top: int = 1):
 
 
 def sessile_drop(nx: int, ny: int, R: float, m: int = 2, n: int = 0, alpha: float = 1.0,
-                 wall: int = 1, lid: int = 1):
-    """Drop of fluid m (radius R) resting on a bottom wall, in fluid n; solid rows
-    at y < wall and y >= ny - lid.  Returns ([C1, C2, C3], solid)."""
+                 wall: int = 1, lid: int = 1, theta0: float = 90.0):
+    """Drop of fluid m resting on a bottom wall, in fluid n; solid rows at
+    y < wall and y >= ny - lid.  The drop is a circular cap of radius R meeting
+    the wall plane y = wall - 1/2 at the angle theta0 (degrees, through the
+    drop; 90 = half disc).  Returns ([C1, C2, C3], solid)."""
     solid = walls_y(nx, ny, wall, lid)
     x, y = _grid2(nx, ny)
-    r = np.hypot(x - nx / 2, y - (wall - 0.5))
+    r = np.hypot(x - nx / 2, y - (wall - 0.5 - R * np.cos(np.radians(theta0))))
     inside = profile(-(r - R), alpha)
     C = [np.zeros((ny, nx)) for _ in range(3)]
     C[m] = inside
@@ -280,3 +282,30 @@ def wells_2d(nx: int = 4096, ny: int = 2048, nwells: int = 32, seed: int = 4):
         c[solid != 0] = 0.0
     return dict(Q=9, nx=nx, ny=ny, nz=1, kappa=(0.01, 0.01, 0.01), alpha=1.0, tau_f=1.0,
                 M_phi=0.1, M_psi=0.1, h=(0.0004, -0.0004, 0.0002), C=[C1, C2, C3], solid=solid)
+
+
+def sweep_wells(count: int = 96, seed: int = 7, ncand: int = 16):
+    """Contact-angle sweep of ``count`` independent D2Q9 square-well lattices of
+    uneven size (Sec. Contact Angles, Fig. 2 settings: kappa = 0.01 each,
+    alpha = 1, tau_f = 1, tau_phi = 1, tau_psi = 2/3 with Gamma = 1, i.e.
+    M_phi = 1/2, M_psi = 1/6).
+
+    Member k: nx = 128 + 32 j, j uniform in {0..20}, ny = nx / 2; floor 8 rows,
+    a well of width uniform in [20, 120] (at most nx - 16) and depth uniform in
+    [10, 60] (clipped to the lattice), filled with fluid 3, fluid 1 below a flat
+    1/2 interface and fluid 2 above.  ``angles`` holds ``ncand`` candidate
+    target pairs (theta_12, theta_13) uniform in [30, 150) degrees; the caller
+    keeps the first pair its wetting inversion accepts and sets ``h`` from it.
+    """
+    out = []
+    for k in range(count):
+        u = uniform(seed * 1000003 + k, 3 + 2 * ncand)
+        nx = 128 + 32 * min(int(21 * u[0]), 20)
+        ny = nx // 2
+        width = min(int(20 + 100 * u[1]), nx - 16)
+        depth = int(10 + 50 * u[2])
+        C, solid = square_well(nx, ny, width, depth, floor=8)
+        angles = [(30 + 120 * u[3 + 2 * j], 30 + 120 * u[4 + 2 * j]) for j in range(ncand)]
+        out.append(dict(Q=9, nx=nx, ny=ny, nz=1, kappa=(0.01, 0.01, 0.01), alpha=1.0, tau_f=1.0,
+                        M_phi=0.5, M_psi=1.0 / 6.0, h=None, C=C, solid=solid, angles=angles))
+    return out
