@@ -243,6 +243,27 @@ tlbm_status tlbm_step_noalloc(tlbm_lattice lattice, tlbm_precision precision, in
                               double M_psi, const double h[3], const uint8_t *solid_dev,
                               const void *src_dev, void *dst_dev, double *mass_dev, void *cuda_stream);
 
+/* ------------------------------------------------------------------ adjoint
+ * Discrete adjoint of the time step (the paper has no counterpart; it serves the
+ * inverse calibration of surface tensions and contact angles).  Loss:
+ *   L = sum over fluid nodes of (C_3(r, T) - target(r))^2
+ * after T = nsteps steps from the equilibrium of the initial fields.  The call
+ * runs the forward steps (keeping a checkpoint every checkpoint_every steps),
+ * then the hand-written adjoint back to the initial fields, recomputing each
+ * segment's states from its checkpoint, and returns the gradient of the
+ * discrete loss (exact up to rounding):
+ *   *loss; dkappa[3] = dL/dkappa_m; dh[3] = dL/dh_m (zero without solid nodes);
+ *   dfields (optional, host [3][N], x fastest) = dL/d(rho, phi, psi) of the
+ *   initial fields at fluid nodes (0 on solid nodes).
+ * target is a host array of N doubles.  Preconditions: TLBM_FP64 storage
+ * (else TLBM_ERR_UNSUPPORTED); the state is the one set by tlbm_init_fields with
+ * no velocity and no step since (else TLBM_ERR_ARG).  Device memory: about
+ * (ceil(nsteps / checkpoint_every) + checkpoint_every + 3) states plus 22
+ * doubles per node (TLBM_ERR_OOM if it does not fit).  Afterwards the engine
+ * holds the state after nsteps steps (tlbm_steps_done advanced by nsteps). */
+tlbm_status tlbm_adjoint_c3_misfit(tlbm *t, int64_t nsteps, int checkpoint_every, const double *target,
+                                   double *loss, double dkappa[3], double dh[3], double *dfields);
+
 /* ------------------------------------------------------------------ wetting theory
  * Host-only functions (no GPU involved) of the model's wetting theory,
  * Sec. Surface Thermodynamics and Sec. Inverting the contact angle relations.

@@ -93,6 +93,7 @@ def _declare(lib):
         "tlbm_batch_last_error": (ctypes.c_char_p, [_H]),
         "tlbm_batch_destroy": (None, [_H]),
         "tlbm_contact_angles": (i, [_dp, d, _dp, _dp]),
+        "tlbm_adjoint_c3_misfit": (i, [_H, i64, i, _dp, _dp, _dp, _dp, _dp]),
         "tlbm_wetting_from_angles": (i, [_dp, d, d, d, _dp]),
     }
     for name, (res, args) in sig.items():
@@ -294,6 +295,20 @@ class TernaryLB:
         buf = np.zeros(self.state_bytes, dtype=np.uint8)
         self._check(self._lib.tlbm_get_state(self._h, buf.ctypes.data_as(_vp), buf.size))
         return buf
+
+    def adjoint_c3_misfit(self, nsteps, checkpoint_every, target, want_fields=True):
+        """Loss sum_fluid (C_3(T) - target)^2 after nsteps from the initial equilibrium
+        and its gradient: (loss, dL/dkappa[3], dL/dh[3], dL/d(rho, phi, psi)[3][N] or
+        None).  Runs forward nsteps (the engine ends there) and the adjoint back."""
+        tg, tp = _arr(target, self.N)
+        loss = ctypes.c_double()
+        dk = np.zeros(3)
+        dh = np.zeros(3)
+        df = np.zeros(3 * self.N) if want_fields else None
+        self._check(self._lib.tlbm_adjoint_c3_misfit(
+            self._h, int(nsteps), int(checkpoint_every), tp, ctypes.byref(loss), dk.ctypes.data_as(_dp),
+            dh.ctypes.data_as(_dp), df.ctypes.data_as(_dp) if df is not None else None))
+        return loss.value, dk, dh, (df.reshape(3, self.N) if df is not None else None)
 
     def set_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)

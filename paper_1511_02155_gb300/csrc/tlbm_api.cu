@@ -21,6 +21,7 @@ struct tlbm {
     int device;
     int kind_req;          // tlbm_kernel requested
     int64_t steps;
+    int rest_init;         // state is the u = 0 equilibrium set by tlbm_init_fields (no step since)
     double kappa[3], alpha, tau_f, M_phi, M_psi, gamma[2], h[3];
     size_t esize;          // bytes per stored population
     size_t tsize;          // bytes per compute value
@@ -329,6 +330,7 @@ tlbm_status tlbm_init_fields(tlbm* t, const double* rho, const double* phi, cons
     CK(cudaMemsetAsync(t->d.flag, 0, sizeof(int), t->st));
     CK(cudaStreamSynchronize(t->st));
     t->steps = 0;
+    t->rest_init = du == nullptr ? 1 : 0;
     return TLBM_OK;
 }
 
@@ -451,6 +453,7 @@ tlbm_status tlbm_set_populations(tlbm* t, const double* host) {
     cudaFree(dv);
     if (e != cudaSuccess) return fail(t, TLBM_ERR_CUDA, "set_populations: %s", cudaGetErrorString(e));
     t->steps = 0;
+    t->rest_init = 0;
     return TLBM_OK;
 }
 
@@ -473,6 +476,79 @@ tlbm_status tlbm_set_state(tlbm* t, const void* host, size_t bytes) {
     CK(cudaMemcpyAsync(t->d.pop[t->d.cur], host, bytes, cudaMemcpyHostToDevice, t->st));
     CK(cudaMemsetAsync(t->d.flag, 0, sizeof(int), t->st));
     CK(cudaStreamSynchronize(t->st));
+    t->rest_init = 0;
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_adjoint_c3_misfit(tlbm* t, int64_t nsteps, int checkpoint_every, const double* target,
+                                   double* loss, double dkappa[3], double dh[3], double* dfields) {
+    if (!t) return TLBM_ERR_ARG;
+    if (nsteps < 1 || checkpoint_every < 1) return fail(t, TLBM_ERR_ARG, "nsteps and checkpoint_every must be >= 1");
+    if (!target || !loss || !dkappa || !dh) return fail(t, TLBM_ERR_ARG, "target, loss, dkappa and dh are required");
+    if (t->d.prec != TLBM_FP64) return fail(t, TLBM_ERR_UNSUPPORTED, "the adjoint needs TLBM_FP64 storage");
+    if (!t->rest_init || t->steps != 0)
+        return fail(t, TLBM_ERR_ARG,
+                    "the adjoint starts from the state of tlbm_init_fields with u = NULL and no step since");
+    tlbm_status s = ensure_mom(t);
+    if (s != TLBM_OK) return s;
+    const int kind = resolve_kind(t);
+    const long long T = nsteps;
+    const int K = (int)(checkpoint_every < nsteps ? checkpoint_every : nsteps);
+    const long long nseg = (T + K - 1) / K;
+    const size_t sb = tlbm_state_bytes(t);
+    const size_t N = (size_t)t->d.N, Np = (size_t)t->d.Np;
+    const int nblk = tlbm_host::mass_blocks();
+    tlbm_host::AdjJob J{};
+    J.nsteps = T;
+    J.K = K;
+    J.state_bytes = sb;
+    void* blocks[9] = {};
+    const size_t sizes[9] = {sb * (size_t)nseg, sb * (size_t)K, sb, sb, sb, sizeof(double) * 18 * Np,
+                             sizeof(double) * 3 * (size_t)nblk, sizeof(double) * 8, sizeof(double) * 4 * N};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 9 && e == cudaSuccess; ++k) e = cudaMalloc(&blocks[k], sizes[k]);
+    auto release = [&]() {
+        for (void* b : blocks) cudaFree(b);
+    };
+    if (e != cudaSuccess) {
+        release();
+        return fail(t, TLBM_ERR_OOM, "adjoint buffers (%zu MB of checkpoints and segment states): %s",
+                    (sizes[0] + sizes[1]) >> 20, cudaGetErrorString(e));
+    }
+    J.ckpt = blocks[0];
+    J.seg = blocks[1];
+    J.fin = blocks[2];
+    J.lam[0] = blocks[3];
+    J.lam[1] = blocks[4];
+    J.work = static_cast<double*>(blocks[5]);
+    J.partials = static_cast<double*>(blocks[6]);
+    J.acc = static_cast<double*>(blocks[7]);
+    double* tgt = static_cast<double*>(blocks[8]);
+    J.target = tgt;
+    J.dfields = tgt + N;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    e = cudaMemsetAsync(J.acc, 0, sizeof(double) * 8, t->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tgt, target, sizeof(double) * N, cudaMemcpyHostToDevice, t->st);
+    if (e == cudaSuccess) e = t->ops->adjoint(t->d, kind, J, t->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(acc, J.acc, sizeof(double) * 8, cudaMemcpyDeviceToHost, t->st);
+    if (e == cudaSuccess && dfields)
+        e = cudaMemcpyAsync(dfields, J.dfields, sizeof(double) * 3 * N, cudaMemcpyDeviceToHost, t->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(t->st);
+    release();
+    if (e != cudaSuccess) return fail(t, TLBM_ERR_CUDA, "adjoint run: %s", cudaGetErrorString(e));
+    t->steps += nsteps;
+    t->rest_init = 0;
+    // wall-normal gradients G_X = (-q1 - q2 - q3, -q1 + q2, -q3), q_m = h_m / (alpha^2 kappa_m)
+    const double a2 = t->alpha * t->alpha;
+    const double dG0 = acc[4], dG1 = acc[5], dG2 = acc[6];
+    const double dq[3] = {-dG0 - dG1, -dG0 + dG1, -dG0 - dG2};
+    *loss = acc[0];
+    for (int m = 0; m < 3; ++m) {
+        const double q = t->h[m] / (a2 * t->kappa[m]);
+        dh[m] = dq[m] / (a2 * t->kappa[m]);
+        dkappa[m] = acc[1 + m] - dq[m] * q / t->kappa[m];
+    }
+    if (!std::isfinite(*loss)) return fail(t, TLBM_ERR_NONFINITE, "non-finite loss");
     return TLBM_OK;
 }
 

@@ -52,6 +52,22 @@ struct BatchState {
     int built;           // descriptors are current
 };
 
+// Buffers of one adjoint run (all device memory, allocated by the caller).
+struct AdjJob {
+    long long nsteps;     // forward steps from the initial equilibrium
+    int K;                // checkpoint interval
+    size_t state_bytes;   // bytes of one population state
+    const double* target; // [N] target C_3
+    void* ckpt;           // ceil(nsteps / K) states: x(0), x(K), ...
+    void* seg;            // min(K, nsteps) states: one recomputed segment
+    void* fin;            // x(nsteps), restored at the end
+    void* lam[2];         // adjoint states (population layout)
+    double* work;         // dX[3], dJ[3], dG[9], dLap[3] node arrays (18 Np)
+    double* partials;     // 3 doubles per block of the fixed grid
+    double* acc;          // [0] loss, [1..3] dL/dkappa (local part), [4..6] dL/dG_X
+    double* dfields;      // [3][N] dL/d(rho, phi, psi) of the initial fields
+};
+
 struct Ops {
     // one time step; flips cur.  When ev0/ev1 are not null they are recorded on
     // the stream just before and just after the step's main kernel(s).
@@ -72,6 +88,9 @@ struct Ops {
     cudaError_t (*batch_build)(BatchState& b, cudaStream_t st);
     // one batched step of every member; ev0/ev1 (if not null) bracket the main kernel
     cudaError_t (*batch_step)(BatchState& b, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
+    // forward run with checkpoints, then the adjoint back to the initial fields
+    // (double storage only; cudaErrorNotSupported otherwise)
+    cudaError_t (*adjoint)(DevState& d, int kind, const AdjJob& job, cudaStream_t st);
 };
 
 // one table per storage format; nullptr if the lattice is not built

@@ -315,7 +315,7 @@ struct NodeEq {
     T Gs[6];
 
     // X = (rho, phi, psi), j = rho u, grad[X][a], lap[X]
-    __device__ __forceinline__ void setup(const Phys<T>& P, T rho_, T jx, T jy, T jz, T phi_,
+    __host__ __device__ __forceinline__ void setup(const Phys<T>& P, T rho_, T jx, T jy, T jz, T phi_,
                                           T psi_, const T (&grad)[3][3], const T (&lap)[3]) {
         rho = rho_; phi = phi_; psi = psi_;
         const T inv = T(1) / rho;
@@ -369,7 +369,7 @@ struct NodeEq {
         }
     }
 
-    __device__ __forceinline__ T eu(int i) const {
+    __host__ __device__ __forceinline__ T eu(int i) const {
         T s = T(0);
         if (Lat<Q>::cx(i)) s += T(Lat<Q>::cx(i)) * ux;
         if (Lat<Q>::cy(i)) s += T(Lat<Q>::cy(i)) * uy;
@@ -377,7 +377,7 @@ struct NodeEq {
         return s;
     }
 
-    __device__ __forceinline__ T grad_term(int i) const {
+    __host__ __device__ __forceinline__ T grad_term(int i) const {
         T s = T(0);
 #pragma unroll
         for (int c = 0; c < 6; ++c)
@@ -386,7 +386,7 @@ struct NodeEq {
     }
 
     // equilibria of direction i >= 1
-    __device__ __forceinline__ void eq(int i, T& fe, T& ge, T& ke) const {
+    __host__ __device__ __forceinline__ void eq(int i, T& fe, T& ge, T& ke) const {
         const T w = T(Lat<Q>::w(i));
         const T e = eu(i);
         const T e2 = T(4.5) * e * e;

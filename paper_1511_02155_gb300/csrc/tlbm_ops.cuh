@@ -2,6 +2,7 @@
 // state into kernel launches.  Included once per precision translation unit.
 #pragma once
 
+#include "tlbm_adjoint.cuh"
 #include "tlbm_fused.cuh"
 #include "tlbm_kernels.cuh"
 
@@ -118,6 +119,93 @@ struct Impl {
 
     static bool has_fused(const DevState& d) { return fused_supported<Q, S>(d); }
 
+    template <bool SOLID>
+    static cudaError_t adjoint_run(DevState& d, int kind, const tlbm_host::AdjJob& J, cudaStream_t st) {
+        const Geom g = geom(d);
+        const Phys<double> P = to_phys<double>(d.phys);
+        double* mom = static_cast<double*>(d.mom);
+        const int grid = grid_for(g.N);
+        const long long Np = g.Np;
+        double *dX = J.work, *dJ = J.work + 3 * Np, *dG = J.work + 6 * Np, *dL = J.work + 15 * Np;
+        auto state = [&](void* base, long long k) { return static_cast<char*>(base) + k * (long long)J.state_bytes; };
+        auto cp = [&](void* dst, const void* src) {
+            return cudaMemcpyAsync(dst, src, J.state_bytes, cudaMemcpyDeviceToDevice, st);
+        };
+        cudaError_t e = cudaSuccess;
+        auto chk = [&](cudaError_t r) {
+            if (e == cudaSuccess && r != cudaSuccess) e = r;
+        };
+        // moments (with wetting ghosts) of state x into mom
+        auto moments_of = [&](const double* x) {
+            k_moments<Q, double, SOLID, true><<<kMassBlocks, kThreads, 0, st>>>(g, x, d.solid, mom, d.partials);
+            if (SOLID) k_ghosts<Q, double><<<grid, kThreads, 0, st>>>(g, d.solid, mom, P);
+        };
+        // node adjoint and stencil transpose (the last stage follows at the call site)
+        auto adjoint_core = [&](const double* x, const double* lam, auto init_tag) {
+            constexpr bool INIT = decltype(init_tag)::value;
+            moments_of(x);
+            k_adj_node<Q, SOLID, INIT><<<kMassBlocks, kThreads, 0, st>>>(g, x, d.solid, mom, lam, P, dX, dJ, dG,
+                                                                          dL, J.partials);
+            k_adj_acc<<<1, kThreads, 0, st>>>(J.partials, kMassBlocks, 3, J.acc + 1);
+            k_adj_gather<Q, SOLID><<<kMassBlocks, kThreads, 0, st>>>(g, d.solid, dX, dG, dL, J.partials);
+            k_adj_acc<<<1, kThreads, 0, st>>>(J.partials, kMassBlocks, 3, J.acc + 4);
+        };
+        const long long T = J.nsteps;
+        const int K = J.K;
+        const long long nseg = (T + K - 1) / K;
+        // forward, checkpoints at multiples of K
+        chk(cp(state(J.ckpt, 0), d.pop[d.cur]));
+        for (long long t = 1; t <= T && e == cudaSuccess; ++t) {
+            chk(step(d, kind, st, nullptr, nullptr));
+            if (t % K == 0 && t < T) chk(cp(state(J.ckpt, t / K), d.pop[d.cur]));
+        }
+        const int curT = d.cur;
+        chk(cp(J.fin, d.pop[d.cur]));
+        // seed: dL/dx(T) of the C_3 misfit
+        k_adj_seed<Q, SOLID><<<kMassBlocks, kThreads, 0, st>>>(g, static_cast<const double*>(J.fin), d.solid,
+                                                                J.target, static_cast<double*>(J.lam[0]),
+                                                                J.partials);
+        k_adj_acc<<<1, kThreads, 0, st>>>(J.partials, kMassBlocks, 1, J.acc);
+        int li = 0;
+        for (long long sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
+            const long long start = sg * K;
+            const long long len = (T - start) < K ? (T - start) : K;
+            chk(cp(d.pop[d.cur], state(J.ckpt, sg)));
+            chk(cp(state(J.seg, 0), d.pop[d.cur]));
+            for (long long k = 1; k < len; ++k) {
+                chk(step(d, kind, st, nullptr, nullptr));
+                chk(cp(state(J.seg, k), d.pop[d.cur]));
+            }
+            for (long long k = len - 1; k >= 0; --k) {
+                const double* x = reinterpret_cast<const double*>(state(J.seg, k));
+                const double* lin = static_cast<const double*>(J.lam[li]);
+                double* lout = static_cast<double*>(J.lam[1 - li]);
+                adjoint_core(x, lin, std::false_type{});
+                k_adj_pull<Q, SOLID, false><<<grid, kThreads, 0, st>>>(g, d.solid, dX, dJ, lin, P, lout, nullptr);
+                li ^= 1;
+            }
+            chk(cudaGetLastError());
+        }
+        // initialisation: x(0) = equilibrium of the fields
+        const double* x0 = reinterpret_cast<const double*>(state(J.ckpt, 0));
+        adjoint_core(x0, static_cast<const double*>(J.lam[li]), std::true_type{});
+        k_adj_pull<Q, SOLID, true><<<grid, kThreads, 0, st>>>(g, d.solid, dX, dJ, nullptr, P, nullptr, J.dfields);
+        // leave the engine at x(T)
+        d.cur = curT;
+        chk(cp(d.pop[d.cur], J.fin));
+        chk(cudaGetLastError());
+        return e;
+    }
+
+    static cudaError_t adjoint(DevState& d, int kind, const tlbm_host::AdjJob& J, cudaStream_t st) {
+        if constexpr (sizeof(S) != 8) {
+            return cudaErrorNotSupported;
+        } else {
+            if (!d.mom) return cudaErrorInvalidValue;
+            return d.solid ? adjoint_run<true>(d, kind, J, st) : adjoint_run<false>(d, kind, J, st);
+        }
+    }
+
     static cudaError_t bbuild(tlbm_host::BatchState& b, cudaStream_t st) { return batch_build<Q, S>(b, st); }
     static cudaError_t bstep(tlbm_host::BatchState& b, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
         return batch_step<Q, S>(b, st, ev0, ev1);
@@ -125,7 +213,7 @@ struct Impl {
 
     static const tlbm_host::Ops* table() {
         static const tlbm_host::Ops o = {&step,     &init,      &fields, &mass,  &get_box, &set_pops,
-                                         &launches, &has_fused, &bbuild, &bstep};
+                                         &launches, &has_fused, &bbuild, &bstep, &adjoint};
         return &o;
     }
 };

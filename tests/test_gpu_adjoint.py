@@ -1,0 +1,175 @@
+"""The GPU adjoint (tlbm_adjoint_c3_misfit) against independent gradients.
+
+- Against the FP64 PyTorch-autograd oracle (oracle/adjoint.py, itself pinned to
+  the C oracle's finite differences): D2Q9 32x16 with a bottom wall and a lid
+  (wetting on), periodic D2Q9 and periodic D3Q19; loss to 1e-12 relative,
+  dL/dkappa and dL/dh to 1e-9 relative, dL/dfields to 1e-9 of their largest
+  magnitude.
+- Against central finite differences (step 1e-4 relative) of the GPU's own FP64
+  forward on the inverse-wetting lattice (D2Q9 256x128, wall at y = 0, lid),
+  300 steps: 1e-5 relative.
+- The checkpoint interval changes nothing (bitwise), the engine ends at the
+  forward state, and the torch.autograd.Function returns the same gradients.
+"""
+import numpy as np
+import pytest
+
+from oracle import adjoint as OA
+import paper_1511_02155_gb300 as tl
+from paper_1511_02155_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU-only machines
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+PAR = dict(alpha=1.0, tau_f=0.9, M_phi=0.3, M_psi=0.2)
+
+
+def _drop_case(nx, ny, R, seed=3, noise=0.05):
+    C, solid = W.sessile_drop(nx, ny, R, m=2, n=0)
+    rho, phi, psi = W.to_aux(*C)
+    for a in (rho, phi, psi):
+        a[solid != 0] = 0.0
+    rng = np.random.default_rng(seed)
+    target = np.clip(psi + noise * rng.standard_normal(psi.shape), 0, 1)
+    return [a.reshape(-1) for a in (rho, phi, psi)], solid.reshape(-1), target.reshape(-1)
+
+
+def _gpu(Q, shape, kap, h, fields, solid, target, T, K):
+    eng = tl.TernaryLB(Q, *shape, kap, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], h, solid, "fp64")
+    eng.init_fields(*fields)
+    out = eng.adjoint_c3_misfit(T, K, target)
+    return eng, out
+
+
+def _compare(got, want):
+    loss, dk, dh, df = got
+    wl, wk, wh, *wf = want
+    assert loss == pytest.approx(wl, rel=1e-12)
+    assert np.allclose(dk, wk, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(wk).max())), (dk, wk)
+    assert np.allclose(dh, wh, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(wh).max())), (dh, wh)
+    for c in range(3):
+        scale = max(np.abs(wf[c]).max(), 1e-30)
+        assert np.abs(df[c] - wf[c]).max() <= 1e-9 * scale, (c, np.abs(df[c] - wf[c]).max() / scale)
+
+
+def test_walls_d2q9_against_autograd_oracle():
+    nx, ny = 32, 16
+    fields, solid, target = _drop_case(nx, ny, 7.0)
+    kap, h = (0.012, 0.02, 0.016), (0.0006, -0.0004, 0.0003)
+    T = 20
+    want = OA.gradients(9, nx, ny, 1, kap, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], h, *fields,
+                        target, T, solid)
+    eng, got = _gpu(9, (nx, ny, 1), kap, h, fields, solid, target, T, 7)
+    _compare(got, want)
+    assert eng.steps_done == T
+    eng.close()
+
+
+def test_periodic_d2q9_and_d3q19_against_autograd_oracle():
+    kap = (0.01, 0.015, 0.02)
+    C = W.lens(24, 20, 5.0, 1.0, 5.0, 15.0, (12.0, 15.0))
+    fields = [a.reshape(-1) for a in W.to_aux(*C)]
+    target = np.roll(fields[2], 3)
+    want = OA.gradients(9, 24, 20, 1, kap, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], (0, 0, 0),
+                        *fields, target, 12)
+    eng, got = _gpu(9, (24, 20, 1), kap, (0, 0, 0), fields, None, target, 12, 5)
+    _compare(got, want)
+    assert np.all(got[2] == 0.0)  # no wall: h does not enter
+    eng.close()
+    n = (8, 6, 5)
+    C = W.spinodal((n[2], n[1], n[0]), seed=4, amp=0.2)
+    fields = [a.reshape(-1) for a in W.to_aux(*C)]
+    target = np.full(fields[2].shape, 1.0 / 3.0)
+    want = OA.gradients(19, *n, kap, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], (0, 0, 0), *fields,
+                        target, 4)
+    eng, got = _gpu(19, n, kap, (0, 0, 0), fields, None, target, 4, 3)
+    _compare(got, want)
+    eng.close()
+
+
+def test_checkpoint_interval_changes_nothing_and_engine_ends_forward():
+    nx, ny = 32, 16
+    fields, solid, target = _drop_case(nx, ny, 7.0)
+    kap, h = (0.012, 0.02, 0.016), (0.0006, -0.0004, 0.0003)
+    res = []
+    for K in (1, 4, 9, 30):
+        eng, out = _gpu(9, (nx, ny, 1), kap, h, fields, solid, target, 9, K)
+        res.append(out)
+        P = eng.get_populations()
+        eng.close()
+    ref = tl.TernaryLB(9, nx, ny, 1, kap, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], h, solid, "fp64")
+    ref.init_fields(*fields)
+    ref.step(9)
+    assert np.array_equal(P, ref.get_populations())
+    ref.close()
+    for r in res[1:]:
+        assert r[0] == res[0][0]
+        for a, b in zip(r[1:], res[0][1:]):
+            assert np.array_equal(a, b)
+
+
+def test_inverse_wetting_lattice_against_finite_differences():
+    nx, ny, T = 256, 128, 300
+    fields, solid, target = _drop_case(nx, ny, 40.0, noise=0.02)
+    kap, h = (0.01, 0.012, 0.014), (0.0005, -0.0003, 0.0002)
+    eng, (loss, dk, dh, _) = _gpu(9, (nx, ny, 1), kap, h, fields, solid, target, T, 50)
+    eng.close()
+
+    def L(k, hh):
+        e = tl.TernaryLB(9, nx, ny, 1, k, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], hh, solid, "fp64")
+        e.init_fields(*fields)
+        e.step(T)
+        C3 = e.fields()["C3"]
+        e.close()
+        d = (C3 - target) * (solid == 0)
+        return float((d * d).sum())
+
+    assert L(kap, h) == pytest.approx(loss, rel=1e-12)
+    for m in range(3):
+        dkm = 1e-4 * kap[m]
+        kp, km = list(kap), list(kap)
+        kp[m] += dkm
+        km[m] -= dkm
+        fd = (L(kp, h) - L(km, h)) / (2 * dkm)
+        assert dk[m] == pytest.approx(fd, rel=1e-5), ("kappa", m, dk[m], fd)
+        dhm = 1e-4 * max(abs(h[m]), 1e-4)
+        hp, hm = list(h), list(h)
+        hp[m] += dhm
+        hm[m] -= dhm
+        fd = (L(kap, hp) - L(kap, hm)) / (2 * dhm)
+        assert dh[m] == pytest.approx(fd, rel=1e-5), ("h", m, dh[m], fd)
+
+
+def test_autograd_function_and_preconditions():
+    from paper_1511_02155_gb300.inverse import c3_misfit
+    nx, ny = 32, 16
+    fields, solid, target = _drop_case(nx, ny, 7.0)
+    kap, h = (0.012, 0.02, 0.016), (0.0006, -0.0004, 0.0003)
+    tk = torch.tensor(kap, dtype=torch.float64, requires_grad=True)
+    th = torch.tensor(h, dtype=torch.float64, requires_grad=True)
+    tf = [torch.tensor(f, requires_grad=True) for f in fields]
+    loss = c3_misfit(tk, th, *tf, torch.tensor(target), nx=nx, ny=ny, solid=solid, nsteps=10,
+                     checkpoint_every=4, **PAR)
+    (2.0 * loss).backward()
+    eng, (l2, dk, dh, df) = _gpu(9, (nx, ny, 1), kap, h, fields, solid, target, 10, 4)
+    eng.close()
+    assert float(loss) == l2
+    assert np.array_equal(tk.grad.numpy(), 2.0 * dk)
+    assert np.array_equal(th.grad.numpy(), 2.0 * dh)
+    for c in range(3):
+        assert np.array_equal(tf[c].grad.numpy(), 2.0 * df[c])
+    # FP32 storage and a stepped state are refused
+    e32 = tl.TernaryLB(9, nx, ny, 1, kap, 1.0, 0.9, 0.3, 0.2, h, solid, "fp32")
+    e32.init_fields(*fields)
+    with pytest.raises(tl.TLBMError):
+        e32.adjoint_c3_misfit(5, 2, target)
+    e32.close()
+    e64 = tl.TernaryLB(9, nx, ny, 1, kap, 1.0, 0.9, 0.3, 0.2, h, solid, "fp64")
+    e64.init_fields(*fields)
+    e64.step(1)
+    with pytest.raises(tl.TLBMError):
+        e64.adjoint_c3_misfit(5, 2, target)
+    e64.close()
