@@ -220,8 +220,10 @@ def gradients(Q, nx, ny, nz, kappa, alpha, tau_f, M_phi, M_psi, h, rho0, phi0, p
     loss, _ = c3_misfit(G, [kap[0], kap[1], kap[2]], [hh[0], hh[1], hh[2]], alpha, tau, gamma,
                         *fields, tgt, nsteps)
     loss.backward()
-    return (float(loss.detach()), kap.grad.numpy().copy(), hh.grad.numpy().copy(),
-            *[f.grad.numpy().copy() for f in fields])
+    def grad_of(t):  # a leaf the loss does not depend on (h without walls) has no gradient: 0
+        return t.grad.numpy().copy() if t.grad is not None else np.zeros(tuple(t.shape))
+
+    return (float(loss.detach()), grad_of(kap), grad_of(hh), *[grad_of(f) for f in fields])
 
 
 def forward_pops(Q, nx, ny, nz, kappa, alpha, tau_f, M_phi, M_psi, h, rho0, phi0, psi0, nsteps,

@@ -156,7 +156,7 @@ def test_autograd_function_and_preconditions():
     (2.0 * loss).backward()
     eng, (l2, dk, dh, df) = _gpu(9, (nx, ny, 1), kap, h, fields, solid, target, 10, 4)
     eng.close()
-    assert float(loss) == l2
+    assert float(loss.detach()) == l2
     assert np.array_equal(tk.grad.numpy(), 2.0 * dk)
     assert np.array_equal(th.grad.numpy(), 2.0 * dh)
     for c in range(3):
