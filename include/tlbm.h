@@ -255,8 +255,10 @@ tlbm_status tlbm_step_noalloc(tlbm_lattice lattice, tlbm_precision precision, in
  *   *loss; dkappa[3] = dL/dkappa_m; dh[3] = dL/dh_m (zero without solid nodes);
  *   dfields (optional, host [3][N], x fastest) = dL/d(rho, phi, psi) of the
  *   initial fields at fluid nodes (0 on solid nodes).
- * target is a host array of N doubles.  Preconditions: TLBM_FP64 storage
- * (else TLBM_ERR_UNSUPPORTED); the state is the one set by tlbm_init_fields with
+ * target is a host array of N doubles.  Preconditions: TLBM_FP64 or TLBM_FP32
+ * storage (else TLBM_ERR_UNSUPPORTED; the adjoint computes in the storage's
+ * precision, the loss and the parameter gradients are summed in FP64); the
+ * state is the one set by tlbm_init_fields with
  * no velocity and no step since (else TLBM_ERR_ARG).  Device memory: about
  * (ceil(nsteps / checkpoint_every) + checkpoint_every + 3) states plus 22
  * doubles per node (TLBM_ERR_OOM if it does not fit).  Afterwards the engine

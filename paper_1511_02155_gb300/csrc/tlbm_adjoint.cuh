@@ -21,7 +21,8 @@
 //                of the pull (a push) -> dL/dx of the previous state
 // The initialisation x(0) = push(eq(fields)) has the same adjoint with omega = 1,
 // no direct term and the pulled lambda; its last stage writes dL/dfields.
-// Only double storage is instantiated (gradient checks need FP64).
+// Instantiated for FP64 and FP32 storage; the loss and the parameter gradients
+// are always accumulated in FP64 (fixed-order block partials).
 #pragma once
 
 #include <type_traits>
@@ -209,10 +210,11 @@ __device__ __forceinline__ void ghost_counts(const Geom& g, const uint8_t* __res
 // Seed of the C_3 misfit L = sum_fluid (C_3(r) - target(r))^2 at state x:
 // dL/dF^k_i(r) = 2 (psi(r) - target(r)), pushed into lam (the pull's transpose);
 // solid nodes' own slots are zeroed.  Loss partials per block (fixed grid).
-template <int Q, bool SOLID>
+template <int Q, typename S, bool SOLID>
 __global__ void __launch_bounds__(kThreads)
-k_adj_seed(Geom g, const double* __restrict__ x, const uint8_t* __restrict__ solid, const double* __restrict__ target,
-           double* __restrict__ lam, double* __restrict__ partials) {
+k_adj_seed(Geom g, const S* __restrict__ x, const uint8_t* __restrict__ solid, const double* __restrict__ target,
+           S* __restrict__ lam, double* __restrict__ partials) {
+    using T = typename Store<S>::T;
     double acc = 0.0;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
          r += (long long)gridDim.x * blockDim.x) {
@@ -222,21 +224,21 @@ k_adj_seed(Geom g, const double* __restrict__ x, const uint8_t* __restrict__ sol
 #pragma unroll
             for (int s = 0; s < 3; ++s)
 #pragma unroll
-                for (int i = 0; i < Q; ++i) pst<Q, double>(lam, g, s, i, xx, yy, zz, 0.0);
+                for (int i = 0; i < Q; ++i) pst<Q, S>(lam, g, s, i, xx, yy, zz, T(0));
             continue;
         }
-        double psi = 0.0;
+        T psi = T(0);
 #pragma unroll
-        for (int i = 0; i < Q; ++i) psi += pull_delta<Q, double, SOLID>(g, x, solid, 2, i, xx, yy, zz);
-        const double d = psi - target[r];
+        for (int i = 0; i < Q; ++i) psi += pull_delta<Q, S, SOLID>(g, x, solid, 2, i, xx, yy, zz);
+        const double d = (double)psi - target[r];
         acc += d * d;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             int xs, ys, zs, is;
             pull_slot<Q, SOLID>(g, solid, i, xx, yy, zz, xs, ys, zs, is);
-            pst<Q, double>(lam, g, 0, is, xs, ys, zs, 0.0);
-            pst<Q, double>(lam, g, 1, is, xs, ys, zs, 0.0);
-            pst<Q, double>(lam, g, 2, is, xs, ys, zs, 2.0 * d);
+            pst<Q, S>(lam, g, 0, is, xs, ys, zs, T(0));
+            pst<Q, S>(lam, g, 1, is, xs, ys, zs, T(0));
+            pst<Q, S>(lam, g, 2, is, xs, ys, zs, T(2.0 * d));
         }
     }
     double z1 = 0.0, z2 = 0.0;
@@ -249,68 +251,71 @@ k_adj_seed(Geom g, const double* __restrict__ x, const uint8_t* __restrict__ sol
 // j = 0, omega = 1, lambda pulled (eq of r was pushed to the pull slots).
 // Outputs node arrays dX[3][Np], dJ[3][Np], dG[9][Np] (dG[3X+a]), dLap[3][Np];
 // kappa partials per block (fixed grid).
-template <int Q, bool SOLID, bool INIT>
+template <int Q, typename S, bool SOLID, bool INIT>
 __global__ void __launch_bounds__(kThreads)
-k_adj_node(Geom g, const double* __restrict__ x, const uint8_t* __restrict__ solid, const double* __restrict__ mom,
-           const double* __restrict__ lam, Phys<double> P, double* __restrict__ dXo, double* __restrict__ dJo,
-           double* __restrict__ dGo, double* __restrict__ dLo, double* __restrict__ partials) {
+k_adj_node(Geom g, const S* __restrict__ x, const uint8_t* __restrict__ solid,
+           const typename Store<S>::T* __restrict__ mom, const S* __restrict__ lam, Phys<typename Store<S>::T> P,
+           typename Store<S>::T* __restrict__ dXo, typename Store<S>::T* __restrict__ dJo,
+           typename Store<S>::T* __restrict__ dGo, typename Store<S>::T* __restrict__ dLo,
+           double* __restrict__ partials) {
+    using T = typename Store<S>::T;
     double k0 = 0.0, k1 = 0.0, k2 = 0.0;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
          r += (long long)gridDim.x * blockDim.x) {
         if (SOLID && solid[r]) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                dXo[c * g.Np + r] = 0.0;
-                dJo[c * g.Np + r] = 0.0;
-                dLo[c * g.Np + r] = 0.0;
+                dXo[c * g.Np + r] = T(0);
+                dJo[c * g.Np + r] = T(0);
+                dLo[c * g.Np + r] = T(0);
             }
 #pragma unroll
-            for (int c = 0; c < 9; ++c) dGo[c * g.Np + r] = 0.0;
+            for (int c = 0; c < 9; ++c) dGo[c * g.Np + r] = T(0);
             continue;
         }
         int xx, yy, zz;
         coords(g, r, xx, yy, zz);
-        double X[3], j[3] = {0.0, 0.0, 0.0}, om[3];
-        double lm[3][Q];
+        T X[3], j[3] = {T(0), T(0), T(0)}, om[3];
+        T lm[3][Q];
         if (INIT) {
             X[0] = mom[r];
             X[1] = mom[g.Np + r];
             X[2] = mom[2 * g.Np + r];
-            om[0] = om[1] = om[2] = 1.0;
+            om[0] = om[1] = om[2] = T(1);
 #pragma unroll
             for (int s = 0; s < 3; ++s)
 #pragma unroll
-                for (int i = 0; i < Q; ++i) lm[s][i] = pull_delta<Q, double, SOLID>(g, lam, solid, s, i, xx, yy, zz);
+                for (int i = 0; i < Q; ++i) lm[s][i] = pull_delta<Q, S, SOLID>(g, lam, solid, s, i, xx, yy, zz);
         } else {
-            X[0] = X[1] = X[2] = 0.0;
+            X[0] = X[1] = X[2] = T(0);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
-                const double f = pull_delta<Q, double, SOLID>(g, x, solid, 0, i, xx, yy, zz);
+                const T f = pull_delta<Q, S, SOLID>(g, x, solid, 0, i, xx, yy, zz);
                 X[0] += f;
-                if (Lat<Q>::cx(i)) j[0] += Lat<Q>::cx(i) * f;
-                if (Lat<Q>::cy(i)) j[1] += Lat<Q>::cy(i) * f;
-                if (Lat<Q>::cz(i)) j[2] += Lat<Q>::cz(i) * f;
-                X[1] += pull_delta<Q, double, SOLID>(g, x, solid, 1, i, xx, yy, zz);
-                X[2] += pull_delta<Q, double, SOLID>(g, x, solid, 2, i, xx, yy, zz);
+                if (Lat<Q>::cx(i)) j[0] += T(Lat<Q>::cx(i)) * f;
+                if (Lat<Q>::cy(i)) j[1] += T(Lat<Q>::cy(i)) * f;
+                if (Lat<Q>::cz(i)) j[2] += T(Lat<Q>::cz(i)) * f;
+                X[1] += pull_delta<Q, S, SOLID>(g, x, solid, 1, i, xx, yy, zz);
+                X[2] += pull_delta<Q, S, SOLID>(g, x, solid, 2, i, xx, yy, zz);
             }
             om[0] = P.omega[0];
             om[1] = P.omega[1];
             om[2] = P.omega[2];
-            const unsigned char* b = reinterpret_cast<const unsigned char*>(lam) + node_off<Q, double>(g, xx, yy, zz);
+            const unsigned char* b = reinterpret_cast<const unsigned char*>(lam) + node_off<Q, S>(g, xx, yy, zz);
 #pragma unroll
             for (int s = 0; s < 3; ++s)
 #pragma unroll
-                for (int i = 0; i < Q; ++i) lm[s][i] = Fmt<Q, double>::ld_delta(b, s, i);
+                for (int i = 0; i < Q; ++i) lm[s][i] = Fmt<Q, S>::ld_delta(b, s, i);
         }
-        double grad[3][3], lap[3];
-        derivs<Q, double>(g, mom, xx, yy, zz, r, grad, lap);
-        double dX[3] = {0.0, 0.0, 0.0}, dJ[3] = {0.0, 0.0, 0.0}, dL[3] = {0.0, 0.0, 0.0};
-        double dG[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
-        double dK[3] = {0.0, 0.0, 0.0};
-        node_adjoint<Q, double>(P, X, j, grad, lap, lm, om, dX, dJ, dG, dL, dK);
-        k0 += dK[0];
-        k1 += dK[1];
-        k2 += dK[2];
+        T grad[3][3], lap[3];
+        derivs<Q, T>(g, mom, xx, yy, zz, r, grad, lap);
+        T dX[3] = {T(0), T(0), T(0)}, dJ[3] = {T(0), T(0), T(0)}, dL[3] = {T(0), T(0), T(0)};
+        T dG[3][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+        T dK[3] = {T(0), T(0), T(0)};
+        node_adjoint<Q, T>(P, X, j, grad, lap, lm, om, dX, dJ, dG, dL, dK);
+        k0 += (double)dK[0];
+        k1 += (double)dK[1];
+        k2 += (double)dK[2];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             dXo[c * g.Np + r] = dX[c];
@@ -332,30 +337,30 @@ k_adj_node(Geom g, const double* __restrict__ x, const uint8_t* __restrict__ sol
 // dX(r) += sum_i [3 w_i e_i . dG(r - e_i) + 6 w_i dLap(r - e_i)] - 6 (1 - w_0) dLap(r).
 // On solid nodes the total is the ghost's adjoint; its share of dL/dG_X
 // (-1, or -sqrt 2 for diagonal-only ghosts) goes to per-block partials.
-template <int Q, bool SOLID>
+template <int Q, typename T, bool SOLID>
 __global__ void __launch_bounds__(kThreads)
-k_adj_gather(Geom g, const uint8_t* __restrict__ solid, double* __restrict__ dX, const double* __restrict__ dG,
-             const double* __restrict__ dL, double* __restrict__ partials) {
+k_adj_gather(Geom g, const uint8_t* __restrict__ solid, T* __restrict__ dX, const T* __restrict__ dG,
+             const T* __restrict__ dL, double* __restrict__ partials) {
     double p0 = 0.0, p1 = 0.0, p2 = 0.0;
-    constexpr double wrest = 1.0 - Lat<Q>::w(0);
+    constexpr T wrest = T(1.0 - Lat<Q>::w(0));
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
          r += (long long)gridDim.x * blockDim.x) {
         int xx, yy, zz;
         coords(g, r, xx, yy, zz);
-        double acc[3];
+        T acc[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] = dX[c * g.Np + r] - 6.0 * wrest * dL[c * g.Np + r];
+        for (int c = 0; c < 3; ++c) acc[c] = dX[c * g.Np + r] - T(6) * wrest * dL[c * g.Np + r];
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const long long b = node(g, wrap(xx - Lat<Q>::cx(i), g.nx), wrap(yy - Lat<Q>::cy(i), g.ny),
                                      wrap(zz - Lat<Q>::cz(i), g.nz));
-            const double w = Lat<Q>::w(i);
+            const T w = T(Lat<Q>::w(i));
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                double s = 6.0 * dL[c * g.Np + b];
-                if (Lat<Q>::cx(i)) s += 3.0 * Lat<Q>::cx(i) * dG[(3 * c + 0) * g.Np + b];
-                if (Lat<Q>::cy(i)) s += 3.0 * Lat<Q>::cy(i) * dG[(3 * c + 1) * g.Np + b];
-                if (Lat<Q>::cz(i)) s += 3.0 * Lat<Q>::cz(i) * dG[(3 * c + 2) * g.Np + b];
+                T s = T(6) * dL[c * g.Np + b];
+                if (Lat<Q>::cx(i)) s += T(3 * Lat<Q>::cx(i)) * dG[(3 * c + 0) * g.Np + b];
+                if (Lat<Q>::cy(i)) s += T(3 * Lat<Q>::cy(i)) * dG[(3 * c + 1) * g.Np + b];
+                if (Lat<Q>::cz(i)) s += T(3 * Lat<Q>::cz(i)) * dG[(3 * c + 2) * g.Np + b];
                 acc[c] += w * s;
             }
         }
@@ -365,9 +370,9 @@ k_adj_gather(Geom g, const uint8_t* __restrict__ solid, double* __restrict__ dX,
             int nax, ndg;
             ghost_counts<Q>(g, solid, xx, yy, zz, nax, ndg);
             const double gc = nax > 0 ? 1.0 : (ndg > 0 ? 1.4142135623730951 : 0.0);
-            p0 -= gc * acc[0];
-            p1 -= gc * acc[1];
-            p2 -= gc * acc[2];
+            p0 -= gc * (double)acc[0];
+            p1 -= gc * (double)acc[1];
+            p2 -= gc * (double)acc[2];
         }
     }
     block_sum3(p0, p1, p2);
@@ -383,11 +388,12 @@ k_adj_gather(Geom g, const uint8_t* __restrict__ solid, double* __restrict__ dX,
 //   STEP: dL/dF_i = (1 - omega) lambda_i + [drho + e_i . dj | dphi | dpsi],
 //         pushed to the pull slots of lam_out (solid nodes' own slots zeroed);
 //   INIT: dL/dfields(r) = dX(r) into dfields[3][N] (solid nodes 0).
-template <int Q, bool SOLID, bool INIT>
+template <int Q, typename S, bool SOLID, bool INIT>
 __global__ void __launch_bounds__(kThreads)
-k_adj_pull(Geom g, const uint8_t* __restrict__ solid, const double* __restrict__ dXt, const double* __restrict__ dJ,
-           const double* __restrict__ lam_in, Phys<double> P, double* __restrict__ lam_out,
-           double* __restrict__ dfields) {
+k_adj_pull(Geom g, const uint8_t* __restrict__ solid, const typename Store<S>::T* __restrict__ dXt,
+           const typename Store<S>::T* __restrict__ dJ, const S* __restrict__ lam_in, Phys<typename Store<S>::T> P,
+           S* __restrict__ lam_out, double* __restrict__ dfields) {
+    using T = typename Store<S>::T;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.N;
          r += (long long)gridDim.x * blockDim.x) {
         int xx, yy, zz;
@@ -401,11 +407,11 @@ k_adj_pull(Geom g, const uint8_t* __restrict__ solid, const double* __restrict__
 #pragma unroll
                 for (int s = 0; s < 3; ++s)
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) pst<Q, double>(lam_out, g, s, i, xx, yy, zz, 0.0);
+                    for (int i = 0; i < Q; ++i) pst<Q, S>(lam_out, g, s, i, xx, yy, zz, T(0));
             }
             continue;
         }
-        double d[3] = {dXt[r], dXt[g.Np + r], dXt[2 * g.Np + r]};
+        T d[3] = {dXt[r], dXt[g.Np + r], dXt[2 * g.Np + r]};
         if (SOLID) {
 #pragma unroll
             for (int i = 1; i < Q; ++i) {
@@ -417,33 +423,33 @@ k_adj_pull(Geom g, const uint8_t* __restrict__ solid, const double* __restrict__
                 ghost_counts<Q>(g, solid, sx, sy, sz, nax, ndg);
                 const bool uses = (i <= Lat<Q>::NAXIS) ? (nax > 0) : (nax == 0 && ndg > 0);
                 if (!uses) continue;
-                const double inv = 1.0 / (i <= Lat<Q>::NAXIS ? nax : ndg);
+                const T inv = T(1) / T(i <= Lat<Q>::NAXIS ? nax : ndg);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) d[c] += dXt[c * g.Np + s] * inv;
             }
         }
         if (INIT) {
-            dfields[r] = d[0];
-            dfields[g.N + r] = d[1];
-            dfields[2 * g.N + r] = d[2];
+            dfields[r] = (double)d[0];
+            dfields[g.N + r] = (double)d[1];
+            dfields[2 * g.N + r] = (double)d[2];
             continue;
         }
-        const double dj[3] = {dJ[r], dJ[g.Np + r], dJ[2 * g.Np + r]};
-        const unsigned char* lb = reinterpret_cast<const unsigned char*>(lam_in) + node_off<Q, double>(g, xx, yy, zz);
+        const T dj[3] = {dJ[r], dJ[g.Np + r], dJ[2 * g.Np + r]};
+        const unsigned char* lb = reinterpret_cast<const unsigned char*>(lam_in) + node_off<Q, S>(g, xx, yy, zz);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            double mf = d[0];
-            if (Lat<Q>::cx(i)) mf += Lat<Q>::cx(i) * dj[0];
-            if (Lat<Q>::cy(i)) mf += Lat<Q>::cy(i) * dj[1];
-            if (Lat<Q>::cz(i)) mf += Lat<Q>::cz(i) * dj[2];
-            const double vf = (1.0 - P.omega[0]) * Fmt<Q, double>::ld_delta(lb, 0, i) + mf;
-            const double vg = (1.0 - P.omega[1]) * Fmt<Q, double>::ld_delta(lb, 1, i) + d[1];
-            const double vk = (1.0 - P.omega[2]) * Fmt<Q, double>::ld_delta(lb, 2, i) + d[2];
+            T mf = d[0];
+            if (Lat<Q>::cx(i)) mf += T(Lat<Q>::cx(i)) * dj[0];
+            if (Lat<Q>::cy(i)) mf += T(Lat<Q>::cy(i)) * dj[1];
+            if (Lat<Q>::cz(i)) mf += T(Lat<Q>::cz(i)) * dj[2];
+            const T vf = (T(1) - P.omega[0]) * Fmt<Q, S>::ld_delta(lb, 0, i) + mf;
+            const T vg = (T(1) - P.omega[1]) * Fmt<Q, S>::ld_delta(lb, 1, i) + d[1];
+            const T vk = (T(1) - P.omega[2]) * Fmt<Q, S>::ld_delta(lb, 2, i) + d[2];
             int xs, ys, zs, is;
             pull_slot<Q, SOLID>(g, solid, i, xx, yy, zz, xs, ys, zs, is);
-            pst<Q, double>(lam_out, g, 0, is, xs, ys, zs, vf);
-            pst<Q, double>(lam_out, g, 1, is, xs, ys, zs, vg);
-            pst<Q, double>(lam_out, g, 2, is, xs, ys, zs, vk);
+            pst<Q, S>(lam_out, g, 0, is, xs, ys, zs, vf);
+            pst<Q, S>(lam_out, g, 1, is, xs, ys, zs, vg);
+            pst<Q, S>(lam_out, g, 2, is, xs, ys, zs, vk);
         }
     }
 }

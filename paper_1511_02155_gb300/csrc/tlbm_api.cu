@@ -485,7 +485,8 @@ tlbm_status tlbm_adjoint_c3_misfit(tlbm* t, int64_t nsteps, int checkpoint_every
     if (!t) return TLBM_ERR_ARG;
     if (nsteps < 1 || checkpoint_every < 1) return fail(t, TLBM_ERR_ARG, "nsteps and checkpoint_every must be >= 1");
     if (!target || !loss || !dkappa || !dh) return fail(t, TLBM_ERR_ARG, "target, loss, dkappa and dh are required");
-    if (t->d.prec != TLBM_FP64) return fail(t, TLBM_ERR_UNSUPPORTED, "the adjoint needs TLBM_FP64 storage");
+    if (t->d.prec != TLBM_FP64 && t->d.prec != TLBM_FP32)
+        return fail(t, TLBM_ERR_UNSUPPORTED, "the adjoint needs TLBM_FP64 or TLBM_FP32 storage");
     if (!t->rest_init || t->steps != 0)
         return fail(t, TLBM_ERR_ARG,
                     "the adjoint starts from the state of tlbm_init_fields with u = NULL and no step since");

@@ -62,7 +62,7 @@ struct AdjJob {
     void* seg;            // min(K, nsteps) states: one recomputed segment
     void* fin;            // x(nsteps), restored at the end
     void* lam[2];         // adjoint states (population layout)
-    double* work;         // dX[3], dJ[3], dG[9], dLap[3] node arrays (18 Np)
+    double* work;         // dX[3], dJ[3], dG[9], dLap[3] node arrays (18 Np values of the compute type)
     double* partials;     // 3 doubles per block of the fixed grid
     double* acc;          // [0] loss, [1..3] dL/dkappa (local part), [4..6] dL/dG_X
     double* dfields;      // [3][N] dL/d(rho, phi, psi) of the initial fields
@@ -89,7 +89,7 @@ struct Ops {
     // one batched step of every member; ev0/ev1 (if not null) bracket the main kernel
     cudaError_t (*batch_step)(BatchState& b, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1);
     // forward run with checkpoints, then the adjoint back to the initial fields
-    // (double storage only; cudaErrorNotSupported otherwise)
+    // (FP64 and FP32 storage; cudaErrorNotSupported for the 16-bit formats)
     cudaError_t (*adjoint)(DevState& d, int kind, const AdjJob& job, cudaStream_t st);
 };
 

@@ -122,11 +122,12 @@ struct Impl {
     template <bool SOLID>
     static cudaError_t adjoint_run(DevState& d, int kind, const tlbm_host::AdjJob& J, cudaStream_t st) {
         const Geom g = geom(d);
-        const Phys<double> P = to_phys<double>(d.phys);
-        double* mom = static_cast<double*>(d.mom);
+        const Phys<T> P = to_phys<T>(d.phys);
+        T* mom = static_cast<T*>(d.mom);
         const int grid = grid_for(g.N);
         const long long Np = g.Np;
-        double *dX = J.work, *dJ = J.work + 3 * Np, *dG = J.work + 6 * Np, *dL = J.work + 15 * Np;
+        T* wk = reinterpret_cast<T*>(J.work);
+        T *dX = wk, *dJ = wk + 3 * Np, *dG = wk + 6 * Np, *dL = wk + 15 * Np;
         auto state = [&](void* base, long long k) { return static_cast<char*>(base) + k * (long long)J.state_bytes; };
         auto cp = [&](void* dst, const void* src) {
             return cudaMemcpyAsync(dst, src, J.state_bytes, cudaMemcpyDeviceToDevice, st);
@@ -136,18 +137,18 @@ struct Impl {
             if (e == cudaSuccess && r != cudaSuccess) e = r;
         };
         // moments (with wetting ghosts) of state x into mom
-        auto moments_of = [&](const double* x) {
-            k_moments<Q, double, SOLID, true><<<kMassBlocks, kThreads, 0, st>>>(g, x, d.solid, mom, d.partials);
-            if (SOLID) k_ghosts<Q, double><<<grid, kThreads, 0, st>>>(g, d.solid, mom, P);
+        auto moments_of = [&](const S* x) {
+            k_moments<Q, S, SOLID, true><<<kMassBlocks, kThreads, 0, st>>>(g, x, d.solid, mom, d.partials);
+            if (SOLID) k_ghosts<Q, T><<<grid, kThreads, 0, st>>>(g, d.solid, mom, P);
         };
         // node adjoint and stencil transpose (the last stage follows at the call site)
-        auto adjoint_core = [&](const double* x, const double* lam, auto init_tag) {
+        auto adjoint_core = [&](const S* x, const S* lam, auto init_tag) {
             constexpr bool INIT = decltype(init_tag)::value;
             moments_of(x);
-            k_adj_node<Q, SOLID, INIT><<<kMassBlocks, kThreads, 0, st>>>(g, x, d.solid, mom, lam, P, dX, dJ, dG,
-                                                                          dL, J.partials);
+            k_adj_node<Q, S, SOLID, INIT><<<kMassBlocks, kThreads, 0, st>>>(g, x, d.solid, mom, lam, P, dX, dJ,
+                                                                             dG, dL, J.partials);
             k_adj_acc<<<1, kThreads, 0, st>>>(J.partials, kMassBlocks, 3, J.acc + 1);
-            k_adj_gather<Q, SOLID><<<kMassBlocks, kThreads, 0, st>>>(g, d.solid, dX, dG, dL, J.partials);
+            k_adj_gather<Q, T, SOLID><<<kMassBlocks, kThreads, 0, st>>>(g, d.solid, dX, dG, dL, J.partials);
             k_adj_acc<<<1, kThreads, 0, st>>>(J.partials, kMassBlocks, 3, J.acc + 4);
         };
         const long long T = J.nsteps;
@@ -162,9 +163,9 @@ struct Impl {
         const int curT = d.cur;
         chk(cp(J.fin, d.pop[d.cur]));
         // seed: dL/dx(T) of the C_3 misfit
-        k_adj_seed<Q, SOLID><<<kMassBlocks, kThreads, 0, st>>>(g, static_cast<const double*>(J.fin), d.solid,
-                                                                J.target, static_cast<double*>(J.lam[0]),
-                                                                J.partials);
+        k_adj_seed<Q, S, SOLID><<<kMassBlocks, kThreads, 0, st>>>(g, static_cast<const S*>(J.fin), d.solid,
+                                                                   J.target, static_cast<S*>(J.lam[0]),
+                                                                   J.partials);
         k_adj_acc<<<1, kThreads, 0, st>>>(J.partials, kMassBlocks, 1, J.acc);
         int li = 0;
         for (long long sg = nseg - 1; sg >= 0 && e == cudaSuccess; --sg) {
@@ -177,19 +178,19 @@ struct Impl {
                 chk(cp(state(J.seg, k), d.pop[d.cur]));
             }
             for (long long k = len - 1; k >= 0; --k) {
-                const double* x = reinterpret_cast<const double*>(state(J.seg, k));
-                const double* lin = static_cast<const double*>(J.lam[li]);
-                double* lout = static_cast<double*>(J.lam[1 - li]);
+                const S* x = reinterpret_cast<const S*>(state(J.seg, k));
+                const S* lin = static_cast<const S*>(J.lam[li]);
+                S* lout = static_cast<S*>(J.lam[1 - li]);
                 adjoint_core(x, lin, std::false_type{});
-                k_adj_pull<Q, SOLID, false><<<grid, kThreads, 0, st>>>(g, d.solid, dX, dJ, lin, P, lout, nullptr);
+                k_adj_pull<Q, S, SOLID, false><<<grid, kThreads, 0, st>>>(g, d.solid, dX, dJ, lin, P, lout, nullptr);
                 li ^= 1;
             }
             chk(cudaGetLastError());
         }
         // initialisation: x(0) = equilibrium of the fields
-        const double* x0 = reinterpret_cast<const double*>(state(J.ckpt, 0));
-        adjoint_core(x0, static_cast<const double*>(J.lam[li]), std::true_type{});
-        k_adj_pull<Q, SOLID, true><<<grid, kThreads, 0, st>>>(g, d.solid, dX, dJ, nullptr, P, nullptr, J.dfields);
+        const S* x0 = reinterpret_cast<const S*>(state(J.ckpt, 0));
+        adjoint_core(x0, static_cast<const S*>(J.lam[li]), std::true_type{});
+        k_adj_pull<Q, S, SOLID, true><<<grid, kThreads, 0, st>>>(g, d.solid, dX, dJ, nullptr, P, nullptr, J.dfields);
         // leave the engine at x(T)
         d.cur = curT;
         chk(cp(d.pop[d.cur], J.fin));
@@ -198,7 +199,7 @@ struct Impl {
     }
 
     static cudaError_t adjoint(DevState& d, int kind, const tlbm_host::AdjJob& J, cudaStream_t st) {
-        if constexpr (sizeof(S) != 8) {
+        if constexpr (Fmt<Q, S>::PACKED) {  // 16-bit formats: no adjoint
             return cudaErrorNotSupported;
         } else {
             if (!d.mom) return cudaErrorInvalidValue;

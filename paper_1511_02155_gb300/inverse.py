@@ -19,14 +19,14 @@ from . import TernaryLB
 
 
 class C3Misfit(torch.autograd.Function):
-    """Loss of the C_3 misfit; gradients from the library's adjoint (FP64 storage)."""
+    """Loss of the C_3 misfit; gradients from the library's adjoint."""
 
     @staticmethod
     def forward(ctx, kappa, h, rho0, phi0, psi0, target, cfg):
         k = [float(v) for v in kappa.detach().cpu().reshape(-1)]
         hh = [float(v) for v in h.detach().cpu().reshape(-1)]
         eng = TernaryLB(cfg["lattice"], cfg["nx"], cfg["ny"], cfg.get("nz", 1), k, cfg["alpha"], cfg["tau_f"],
-                        cfg["M_phi"], cfg["M_psi"], hh, cfg.get("solid"), "fp64")
+                        cfg["M_phi"], cfg["M_psi"], hh, cfg.get("solid"), cfg.get("precision", "fp64"))
         try:
             f = [t.detach().cpu().double().numpy().reshape(-1) for t in (rho0, phi0, psi0)]
             eng.init_fields(*f)
@@ -51,9 +51,10 @@ class C3Misfit(torch.autograd.Function):
 
 
 def c3_misfit(kappa, h, rho0, phi0, psi0, target, *, lattice=9, nx, ny, nz=1, alpha=1.0, tau_f=1.0, M_phi=0.1,
-              M_psi=0.1, solid=None, nsteps, checkpoint_every=100):
-    """Differentiable C_3 misfit (see the module docstring)."""
+              M_psi=0.1, solid=None, nsteps, checkpoint_every=100, precision="fp64"):
+    """Differentiable C_3 misfit (see the module docstring); precision "fp64" or
+    "fp32" (the adjoint then runs in FP32 with FP64 parameter sums)."""
     cfg = dict(lattice=lattice, nx=nx, ny=ny, nz=nz, alpha=alpha, tau_f=tau_f, M_phi=M_phi, M_psi=M_psi,
                solid=None if solid is None else np.asarray(solid).reshape(-1), nsteps=nsteps,
-               checkpoint_every=checkpoint_every)
+               checkpoint_every=checkpoint_every, precision=precision)
     return C3Misfit.apply(kappa, h, rho0, phi0, psi0, target, cfg)

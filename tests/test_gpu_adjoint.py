@@ -10,6 +10,10 @@
   300 steps: 1e-5 relative.
 - The checkpoint interval changes nothing (bitwise), the engine ends at the
   forward state, and the torch.autograd.Function returns the same gradients.
+- FP32 storage (adjoint in FP32, loss and parameter gradients summed in FP64)
+  against the FP64 adjoint: loss to 1e-5 relative, dL/dkappa and dL/dh to 1e-3
+  relative, dL/dfields to 1e-3 of their largest magnitude (D2Q9 with walls,
+  20 and 300 steps; FP32 rounding of the forward and backward sweeps).
 """
 import numpy as np
 import pytest
@@ -37,8 +41,8 @@ def _drop_case(nx, ny, R, seed=3, noise=0.05):
     return [a.reshape(-1) for a in (rho, phi, psi)], solid.reshape(-1), target.reshape(-1)
 
 
-def _gpu(Q, shape, kap, h, fields, solid, target, T, K):
-    eng = tl.TernaryLB(Q, *shape, kap, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], h, solid, "fp64")
+def _gpu(Q, shape, kap, h, fields, solid, target, T, K, prec="fp64"):
+    eng = tl.TernaryLB(Q, *shape, kap, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], h, solid, prec)
     eng.init_fields(*fields)
     out = eng.adjoint_c3_misfit(T, K, target)
     return eng, out
@@ -161,15 +165,33 @@ def test_autograd_function_and_preconditions():
     assert np.array_equal(th.grad.numpy(), 2.0 * dh)
     for c in range(3):
         assert np.array_equal(tf[c].grad.numpy(), 2.0 * df[c])
-    # FP32 storage and a stepped state are refused
-    e32 = tl.TernaryLB(9, nx, ny, 1, kap, 1.0, 0.9, 0.3, 0.2, h, solid, "fp32")
-    e32.init_fields(*fields)
+    # 16-bit storage and a stepped state are refused
+    e16 = tl.TernaryLB(9, nx, ny, 1, kap, 1.0, 0.9, 0.3, 0.2, h, solid, "fp16")
+    e16.init_fields(*fields)
     with pytest.raises(tl.TLBMError):
-        e32.adjoint_c3_misfit(5, 2, target)
-    e32.close()
+        e16.adjoint_c3_misfit(5, 2, target)
+    e16.close()
     e64 = tl.TernaryLB(9, nx, ny, 1, kap, 1.0, 0.9, 0.3, 0.2, h, solid, "fp64")
     e64.init_fields(*fields)
     e64.step(1)
     with pytest.raises(tl.TLBMError):
         e64.adjoint_c3_misfit(5, 2, target)
     e64.close()
+
+
+@pytest.mark.parametrize("shape,T,R", [((32, 16), 20, 7.0), ((256, 128), 300, 40.0)])
+def test_fp32_adjoint_against_fp64(shape, T, R):
+    nx, ny = shape
+    fields, solid, target = _drop_case(nx, ny, R, noise=0.02)
+    kap, h = (0.01, 0.012, 0.014), (0.0005, -0.0003, 0.0002)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        eng, out[prec] = _gpu(9, (nx, ny, 1), kap, h, fields, solid, target, T, 50, prec)
+        eng.close()
+    (l64, k64, h64, f64), (l32, k32, h32, f32) = out["fp64"], out["fp32"]
+    print(f"{nx}x{ny} T={T}: loss {l64:.8e} vs {l32:.8e}; dkappa {k64} vs {k32}; dh {h64} vs {h32}")
+    assert l32 == pytest.approx(l64, rel=1e-5)
+    assert np.allclose(k32, k64, rtol=1e-3, atol=1e-3 * np.abs(k64).max())
+    assert np.allclose(h32, h64, rtol=1e-3, atol=1e-3 * np.abs(h64).max())
+    for c in range(3):
+        assert np.abs(f32[c] - f64[c]).max() <= 1e-3 * np.abs(f64[c]).max()
