@@ -340,7 +340,7 @@ def run_sweep(args):
     alg_bytes = bpn * n_fluid + N
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    tag = f"batch:sweep96:{args.precision}:{tile[0]},{tile[1]}"
+    tag = f"batch:sweep96:{args.precision}"  # captured at the tile the autotuner chose in that run
     traffic = traffic_from_profiles(tag, kernel_source_digest(), N)
 
     # end to end: upload every member's fields from pinned host memory, K batched
