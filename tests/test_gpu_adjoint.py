@@ -2,7 +2,8 @@
 
 - Against the FP64 PyTorch-autograd oracle (oracle/adjoint.py, itself pinned to
   the C oracle's finite differences): D2Q9 32x16 with a bottom wall and a lid
-  (wetting on), periodic D2Q9 and periodic D3Q19; loss to 1e-12 relative,
+  (wetting on), D3Q19 with walls and a step, periodic D2Q9 and periodic
+  D3Q19; loss to 1e-12 relative,
   dL/dkappa and dL/dh to 1e-9 relative, dL/dfields to 1e-9 of their largest
   magnitude.
 - Against central finite differences (step 1e-4 relative) of the GPU's own FP64
@@ -90,6 +91,27 @@ def test_periodic_d2q9_and_d3q19_against_autograd_oracle():
     want = OA.gradients(19, *n, kap, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], (0, 0, 0), *fields,
                         target, 4)
     eng, got = _gpu(19, n, kap, (0, 0, 0), fields, None, target, 4, 3)
+    _compare(got, want)
+    eng.close()
+
+
+def test_walls_d3q19_against_autograd_oracle():
+    nx, ny, nz = 8, 7, 6
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, ny - 1, :] = 1
+    solid[1:3, 1, 2:4] = 1  # a step on the bottom wall (edges and corners)
+    C = W.spinodal((nz, ny, nx), seed=6, amp=0.2)
+    rho, phi, psi = W.to_aux(*C)
+    for a in (rho, phi, psi):
+        a[solid != 0] = 0.0
+    fields = [a.reshape(-1) for a in (rho, phi, psi)]
+    solid = solid.reshape(-1)
+    target = np.full(fields[2].shape, 0.3) * (solid == 0)
+    kap, h = (0.012, 0.02, 0.016), (0.0006, -0.0004, 0.0003)
+    want = OA.gradients(19, nx, ny, nz, kap, PAR["alpha"], PAR["tau_f"], PAR["M_phi"], PAR["M_psi"], h, *fields,
+                        target, 5, solid)
+    eng, got = _gpu(19, (nx, ny, nz), kap, h, fields, solid, target, 5, 2)
     _compare(got, want)
     eng.close()
 
