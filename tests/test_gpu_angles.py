@@ -15,8 +15,8 @@ paper's Fig. 2 settings):
   near-constant factor of about 1.05, so the deviation grows toward the ends of
   the range (about 5 degrees at 150, 11 at 160); the paper reports at most
   4 degrees over 14..166.
-- FP32 and FP64 storage give angles within 0.5 degrees of each other (the FP64
-  engine itself matches the FP64 oracle to 1e-12).
+- FP32, FP16 and BF16 storage give angles within 0.5 degrees of FP64 (the
+  FP64 engine itself matches the FP64 oracle to 1e-12).
 """
 import numpy as np
 import pytest
@@ -70,13 +70,14 @@ def test_sessile_drop_angles_follow_young():
         e.close()
 
 
-def test_fp32_and_fp64_angles_agree():
+def test_storage_precisions_give_the_same_angles():
     out = {}
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp64", "fp16", "bf16"):
         engines = [_drop(t, t, prec) for t in (60.0, 120.0)]
         with tl.TernaryBatch(engines) as b:
             b.set_graph(True)
             b.step(40000)
         out[prec] = [_angle(e) for e in engines]
-    print("fp32", out["fp32"], "fp64", out["fp64"])
-    assert np.max(np.abs(np.subtract(out["fp32"], out["fp64"]))) <= 0.5
+    print(out)
+    for prec in ("fp32", "fp16", "bf16"):
+        assert np.max(np.abs(np.subtract(out[prec], out["fp64"]))) <= 0.5, prec
