@@ -221,8 +221,13 @@ def test_fp32_adjoint_against_fp64(shape, T, R):
 
 def test_gradient_descent_recovers_hidden_wetting_parameters():
     """Inverse wetting with the autograd wrapper: a target C_3 field made with
-    hidden h*, a start 40 % away, and plain gradient steps on h (scaled by the
-    initial gradient); the misfit and the distance to h* both fall."""
+    hidden h*, a start 40 % away (contact angles 3-7 degrees off), and L-BFGS-B
+    (scipy) driven by the adjoint's gradient: the misfit falls by 100x and the
+    recovered h gives the hidden contact angles to 0.5 degrees.  (h itself is
+    determined only up to the direction that leaves every angle unchanged --
+    only differences of solid-fluid tensions enter, Sec. Inverting the contact
+    angle relations -- so the angles, not h, are compared.)"""
+    optimize = pytest.importorskip("scipy.optimize")
     from paper_1511_02155_gb300.inverse import c3_misfit
     nx, ny, T = 64, 32, 400
     fields, solid, _ = _drop_case(nx, ny, 12.0)
@@ -236,19 +241,21 @@ def test_gradient_descent_recovers_hidden_wetting_parameters():
     eng.close()
     tk = torch.tensor(kap, dtype=torch.float64)
     tf = [torch.tensor(f) for f in fields]
-    h = torch.tensor(h_star * 1.4, dtype=torch.float64, requires_grad=True)
-    losses, dists = [], []
-    lr = None
-    for _ in range(8):
+    scale = 1e-3  # optimise u = h / scale
+
+    def fun(u):
+        h = torch.tensor(u * scale, dtype=torch.float64, requires_grad=True)
         loss = c3_misfit(tk, h, *tf, target, nx=nx, ny=ny, solid=solid, nsteps=T, checkpoint_every=100, **PAR)
-        h.grad = None
         loss.backward()
-        if lr is None:  # first step moves h by 20 % of its size
-            lr = 0.2 * float(h.detach().norm()) / float(h.grad.norm())
-        losses.append(float(loss.detach()))
-        dists.append(float((h.detach() - torch.tensor(h_star)).norm()))
-        with torch.no_grad():
-            h -= lr * h.grad
-    print("losses", losses, "distance to h*", dists)
-    assert losses[-1] < 0.25 * losses[0]
-    assert dists[-1] < 0.5 * dists[0]
+        return float(loss.detach()), h.grad.numpy() * scale
+
+    u0 = h_star * 1.4 / scale
+    l0 = fun(u0)[0]
+    bounds = [(-0.2 * k / scale, 0.2 * k / scale) for k in kap]  # |4 h| < 0.8 alpha kappa
+    res = optimize.minimize(fun, u0, jac=True, method="L-BFGS-B", bounds=bounds, options={"maxiter": 25})
+    h = res.x * scale
+    print("loss", l0, "->", res.fun, "h", h, "h*", h_star, "evaluations", res.nfev)
+    assert res.fun < 0.01 * l0
+    got, want = tl.contact_angles(kap, PAR["alpha"], h), tl.contact_angles(kap, PAR["alpha"], h_star)
+    print("angles", got, "hidden", want)
+    assert np.max(np.abs(np.subtract(got, want))) <= 0.5
