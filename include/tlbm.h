@@ -261,8 +261,10 @@ tlbm_status tlbm_step_noalloc(tlbm_lattice lattice, tlbm_precision precision, in
  * state is the one set by tlbm_init_fields with
  * no velocity and no step since (else TLBM_ERR_ARG).  Device memory: about
  * (ceil(nsteps / checkpoint_every) + checkpoint_every + 3) states plus 22
- * doubles per node (TLBM_ERR_OOM if it does not fit).  Afterwards the engine
- * holds the state after nsteps steps (tlbm_steps_done advanced by nsteps). */
+ * doubles per node (TLBM_ERR_OOM if it does not fit; nothing is run then).
+ * Afterwards the engine holds the state after nsteps steps (tlbm_steps_done
+ * advanced by nsteps).  If a CUDA error interrupts the run, the engine's
+ * populations are unspecified: set them again (tlbm_init_fields) before use. */
 tlbm_status tlbm_adjoint_c3_misfit(tlbm *t, int64_t nsteps, int checkpoint_every, const double *target,
                                    double *loss, double dkappa[3], double dh[3], double *dfields);
 
