@@ -194,3 +194,27 @@ def test_periodic_tile_without_a_batched_kernel_is_refused():
         b.set_tile(0, 1)  # one plane per block
         assert b.blocks > blocks
         b.step(2)
+
+
+@pytest.mark.parametrize("variant,chunk", [(0, 0), (2, 0), (3, 16), (1, 5)])
+def test_single_member_batch_at_every_solid_tile_equals_lone_engine(variant, chunk):
+    batched, lone = _pairs("wells", "fp32")
+    with tl.TernaryBatch(batched[1:2]) as b:
+        b.set_tile(variant, chunk)
+        b.set_graph(True)
+        b.step(6)
+        lone[1].step(6)
+        assert np.array_equal(batched[1].get_populations(), lone[1].get_populations())
+
+
+def test_autotune_on_d3q19_keeps_results():
+    batched, lone = _pairs("spinodal3d", "fp32")
+    with tl.TernaryBatch(batched) as b:
+        variant, chunk = b.autotune(trial_steps=1)
+        assert variant == 0  # one batched shape for periodic D3Q19
+        n = batched[0].steps_done
+        b.step(2)
+        for e in lone:
+            e.step(n + 2)
+        for eb, el in zip(batched, lone):
+            assert np.array_equal(eb.get_populations(), el.get_populations())
