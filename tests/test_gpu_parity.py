@@ -254,6 +254,30 @@ def test_full_size_spinodal_256_cubed_fp32_sampled_step():
     assert np.all(np.abs(m1 - m0) <= 1e-6 * np.abs(m0).max())
 
 
+def test_full_size_wells_4096_fp32_sampled_step():
+    """The benchmark's walls-and-wetting workload (D2Q9 4096x2048, 32 wells), in
+    the benchmark's launch configuration (solid-aware fused kernel): patches
+    over wells, walls, the lid and the 1/2 interface."""
+    cfg = W.wells_2d()
+    nx, ny = cfg["nx"], cfg["ny"]
+    solid = cfg["solid"]
+    rho, phi, psi = W.to_aux(*cfg["C"])
+    for a in (rho, phi, psi):
+        a[solid != 0] = 0.0
+    eng = tl.TernaryLB(9, nx, ny, 1, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"], cfg["M_psi"],
+                       cfg["h"], solid.reshape(-1), "fp32")
+    assert eng.kernel == "fused"
+    eng.init_fields(rho, phi, psi)
+    eng.step(200)
+    p = oracle.make_params(9, nx, ny, 1, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"], cfg["M_psi"],
+                           cfg["h"])
+    pitch = nx // 32
+    centres = [(k * pitch + pitch // 2, 40, 0) for k in (0, 7, 19, 31)]      # inside / at the rim of wells
+    centres += [(k * pitch + 5, 30, 0) for k in (3, 12)]                      # well side walls and corners
+    centres += [(1000, ny - 6, 0), (2500, 48 + (ny - 49) // 2, 0), (nx - 2, 50, 0)]  # lid, interface, wrap
+    _patch_step_check(eng, p, solid.reshape(-1), centres, 24, 2e-6)
+
+
 def test_full_size_2d_probe_8192_fp32_sampled_step():
     n = 8192
     C = W.spinodal((n, n), seed=5)
