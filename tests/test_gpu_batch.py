@@ -218,3 +218,37 @@ def test_autotune_on_d3q19_keeps_results():
             e.step(n + 2)
         for eb, el in zip(batched, lone):
             assert np.array_equal(eb.get_populations(), el.get_populations())
+
+
+def test_sweep_members_batched_equal_lone_engines():
+    """Members of the benchmark's 96-lattice contact-angle sweep (their own sizes,
+    wells and wetting parameters from the library's inversion), batched under a
+    graph at the autotuned tile, against the same lattices stepped alone."""
+    members = W.sweep_wells(96)[:8]
+    engines, lone = [], []
+    for m in members:
+        h = None
+        for a in m["angles"]:
+            try:
+                h = tl.wetting_from_angles(m["kappa"], m["alpha"], *a)
+                break
+            except tl.TLBMError:
+                continue
+        rho, phi, psi = W.to_aux(*m["C"])
+        for arr in (rho, phi, psi):
+            arr[m["solid"] != 0] = 0.0
+        for group in (engines, lone):
+            e = tl.TernaryLB(9, m["nx"], m["ny"], 1, m["kappa"], m["alpha"], m["tau_f"], m["M_phi"], m["M_psi"],
+                             h, m["solid"], "fp32")
+            e.init_fields(rho, phi, psi)
+            group.append(e)
+    with tl.TernaryBatch(engines) as b:
+        variant, chunk = b.autotune(trial_steps=1)
+        b.set_graph(True)
+        b.step(5)
+        for e in lone:
+            e.set_tile(variant, chunk)
+            e.step(engines[0].steps_done)
+        for eb, el in zip(engines, lone):
+            assert np.array_equal(eb.get_populations(), el.get_populations())
+            assert np.array_equal(eb.step_mass(), el.step_mass())
