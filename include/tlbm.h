@@ -296,6 +296,8 @@ tlbm_status tlbm_wetting_from_angles(const double kappa[3], double alpha, double
                                      double theta13_deg, double h[3]);
 
 /* ------------------------------------------------------------------ batches
+ * The paper has no counterpart: this is an execution feature for parameter
+ * sweeps such as the contact-angle runs of Sec. Contact Angles.
  * Many independent lattices of one lattice type and storage format (for example
  * a contact-angle or kappa sweep over lattices of uneven size) advanced by ONE
  * kernel launch per step plus one launch for all their FP64 totals.  A batch
