@@ -210,10 +210,10 @@ int tlbm_launches_per_step(const tlbm *t);
 /*
  * One time step on caller-owned device buffers, allocating nothing.
  * The paper has no counterpart: this is an engineering entry point for callers
- * that may not allocate device memory themselves -- code embedded in a host
- * framework that owns every device allocation through its own pool, loops that
- * must not pay allocation latency, and code running where cudaMalloc is not
- * allowed (while a stream is being captured into a CUDA graph).
+ * that may not allocate device memory themselves -- a plug-in inside a host
+ * framework that owns every device allocation through its own pool and budget
+ * (a cudaMalloc behind its back would break its accounting or fail), and
+ * real-time loops that must not pay allocation latency or fragment memory.
  *   lattice, nx, ny, nz, kappa, alpha, tau_f, M_phi, M_psi, h: as tlbm_create
  *                 (Gamma_phi = Gamma_psi = 1).
  *   precision     TLBM_FP32 or TLBM_FP64 only.
@@ -223,9 +223,13 @@ int tlbm_launches_per_step(const tlbm *t);
  *   dst_dev       device buffer of the same size; receives the state one step
  *                 later.  Must not overlap src_dev.
  *   mass_dev      device array of 3 doubles for the FP64 totals of the input
- *                 state (sum rho, phi, psi over fluid nodes), or NULL.
+ *                 state (sum rho, phi, psi over fluid nodes), or NULL.  A state
+ *                 that has blown up shows as non-finite totals here (there is no
+ *                 other non-finite report).
  *   cuda_stream   stream to run on (NULL = default stream).
- * The step is the split implementation (moments, ghosts, collide + stream).
+ * The step is the engine's split implementation (moments, ghosts, collide +
+ * stream), the same kernels and parameters tlbm_step runs under
+ * TLBM_KERNEL_SPLIT.
  * Its intermediate arrays live in one fixed 8 MiB __device__ buffer per device,
  * which limits the lattice to 349504 nodes in FP64 and 699008 nodes in FP32;
  * larger lattices return TLBM_ERR_ARG before any device work.  Every GPU that

@@ -1,10 +1,11 @@
 """In-tree build of ``libtlbm.so`` (the C ABI of include/tlbm.h) for sm_103a.
 
-Each storage format is its own translation unit so that the FP64 unit can be
-compiled without fused multiply-add contraction (``-fmad=false``), which keeps
-its arithmetic in the same rounding steps as a plain IEEE evaluation; the FP32
-and 16-bit units keep FMA.  The units compile in parallel and link with the
-static CUDA runtime into one shared library next to this file.
+Each storage format and lattice is its own translation unit, so that the FP64
+units can be compiled without fused multiply-add contraction (``-fmad=false``),
+which keeps their arithmetic in the same rounding steps as a plain IEEE
+evaluation, while the FP32 and 16-bit units keep FMA; no two units instantiate
+the same kernel.  The units compile in parallel and link with the static CUDA
+runtime into one shared library next to this file.
 """
 from __future__ import annotations
 
@@ -22,11 +23,15 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {
     "tlbm_api.cu": [],
-    "tlbm_f64.cu": ["-fmad=false"],
-    "tlbm_f32.cu": [],
-    "tlbm_f16.cu": [],
-    "tlbm_bf16.cu": [],
-    "tlbm_noalloc.cu": ["-fmad=false"],
+    "tlbm_f64_q9.cu": ["-fmad=false"],
+    "tlbm_f64_q19.cu": ["-fmad=false"],
+    "tlbm_f32_q9.cu": [],
+    "tlbm_f32_q19.cu": [],
+    "tlbm_f16_q9.cu": [],
+    "tlbm_f16_q19.cu": [],
+    "tlbm_bf16_q9.cu": [],
+    "tlbm_bf16_q19.cu": [],
+    "tlbm_noalloc.cu": [],
     "tlbm_wetting.cpp": [],
 }
 

@@ -57,29 +57,7 @@ tlbm_status fail(tlbm* t, tlbm_status s, const char* fmt, ...) {
                         "%s failed: %s", #call, cudaGetErrorString(e_));                      \
     } while (0)
 
-void set_phys(tlbm* t) {
-    auto& p = t->d.phys;
-    const double k1 = t->kappa[0], k2 = t->kappa[1], k3 = t->kappa[2];
-    for (int m = 0; m < 3; ++m) p.kappa[m] = t->kappa[m];
-    p.a2 = t->alpha * t->alpha;
-    p.omega[0] = 1.0 / t->tau_f;
-    p.omega[1] = 1.0 / (0.5 + t->M_phi / t->gamma[0]);
-    p.omega[2] = 1.0 / (0.5 + t->M_psi / t->gamma[1]);
-    p.gamma[0] = t->gamma[0];
-    p.gamma[1] = t->gamma[1];
-    // wall-normal gradients of rho, phi, psi (wetting conditions on the auxiliary fields)
-    const double q1 = t->h[0] / (p.a2 * k1), q2 = t->h[1] / (p.a2 * k2), q3 = t->h[2] / (p.a2 * k3);
-    p.Gw[0] = -q1 - q2 - q3;
-    p.Gw[1] = -q1 + q2;
-    p.Gw[2] = -q3;
-    // mixing coefficients of the pressure tensor
-    p.K[0][0] = (k1 + k2) / 4.0;
-    p.K[1][1] = (k1 + k2) / 4.0;
-    p.K[2][2] = (k1 + k2 + 4.0 * k3) / 4.0;
-    p.K[0][1] = p.K[1][0] = (k1 - k2) / 4.0;
-    p.K[1][2] = p.K[2][1] = -(k1 - k2) / 4.0;
-    p.K[0][2] = p.K[2][0] = -(k1 + k2) / 4.0;
-}
+void set_phys(tlbm* t) { t->d.phys = tlbm_host::make_phys(t->kappa, t->alpha, t->tau_f, t->M_phi, t->M_psi, t->gamma, t->h); }
 
 int resolve_kind(const tlbm* t) {
     if (t->kind_req == TLBM_KERNEL_SPLIT) return tlbm_host::KIND_SPLIT;
@@ -102,7 +80,46 @@ tlbm_status ensure_mom(tlbm* t) {
 }  // namespace
 
 namespace tlbm_host {
-int mass_blocks() { return 1216; }
+int mass_blocks() { return kMassBlocks; }
+
+PhysD make_phys(const double kappa[3], double alpha, double tau_f, double M_phi, double M_psi,
+                const double gamma[2], const double h[3]) {
+    PhysD p;
+    const double k1 = kappa[0], k2 = kappa[1], k3 = kappa[2];
+    for (int m = 0; m < 3; ++m) p.kappa[m] = kappa[m];
+    p.a2 = alpha * alpha;
+    // BGK rates: tau_phi = 1/2 + M_phi / Gamma_phi, tau_psi likewise (Eqs. Mobility1/2)
+    p.omega[0] = 1.0 / tau_f;
+    p.omega[1] = 1.0 / (0.5 + M_phi / gamma[0]);
+    p.omega[2] = 1.0 / (0.5 + M_psi / gamma[1]);
+    p.gamma[0] = gamma[0];
+    p.gamma[1] = gamma[1];
+    // wall-normal gradients of rho, phi, psi (wetting conditions on the auxiliary fields)
+    const double q1 = h[0] / (p.a2 * k1), q2 = h[1] / (p.a2 * k2), q3 = h[2] / (p.a2 * k3);
+    p.Gw[0] = -q1 - q2 - q3;
+    p.Gw[1] = -q1 + q2;
+    p.Gw[2] = -q3;
+    // mixing coefficients of the pressure tensor
+    p.K[0][0] = (k1 + k2) / 4.0;
+    p.K[1][1] = (k1 + k2) / 4.0;
+    p.K[2][2] = (k1 + k2 + 4.0 * k3) / 4.0;
+    p.K[0][1] = p.K[1][0] = (k1 - k2) / 4.0;
+    p.K[1][2] = p.K[2][1] = -(k1 - k2) / 4.0;
+    p.K[0][2] = p.K[2][0] = -(k1 + k2) / 4.0;
+    return p;
+}
+
+const Ops* ops_for(int precision, int Q) {
+    if (Q != 9 && Q != 19) return nullptr;
+    const bool q9 = Q == 9;
+    switch (precision) {
+        case TLBM_FP64: return q9 ? ops_fp64_q9() : ops_fp64_q19();
+        case TLBM_FP32: return q9 ? ops_fp32_q9() : ops_fp32_q19();
+        case TLBM_FP16_OFFSET: return q9 ? ops_fp16_q9() : ops_fp16_q19();
+        case TLBM_BF16_OFFSET: return q9 ? ops_bf16_q9() : ops_bf16_q19();
+    }
+    return nullptr;
+}
 }  // namespace tlbm_host
 
 extern "C" {
@@ -178,12 +195,13 @@ tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz
     const Ops* ops = nullptr;
     size_t esize = 0, tsize = 0;
     switch (precision) {
-        case TLBM_FP64: ops = tlbm_host::ops_fp64(lattice); esize = 8; tsize = 8; break;
-        case TLBM_FP32: ops = tlbm_host::ops_fp32(lattice); esize = 4; tsize = 4; break;
-        case TLBM_FP16_OFFSET: ops = tlbm_host::ops_fp16(lattice); esize = 2; tsize = 4; break;
-        case TLBM_BF16_OFFSET: ops = tlbm_host::ops_bf16(lattice); esize = 2; tsize = 4; break;
+        case TLBM_FP64: esize = 8; tsize = 8; break;
+        case TLBM_FP32: esize = 4; tsize = 4; break;
+        case TLBM_FP16_OFFSET: esize = 2; tsize = 4; break;
+        case TLBM_BF16_OFFSET: esize = 2; tsize = 4; break;
         default: return fail(nullptr, TLBM_ERR_ARG, "unknown precision");
     }
+    ops = tlbm_host::ops_for(precision, lattice);
     if (!ops) return fail(nullptr, TLBM_ERR_UNSUPPORTED, "precision/lattice combination not built");
 
     t = new tlbm();
@@ -203,6 +221,10 @@ tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz
     t->kernel_steps = 0;
     cudaGetDevice(&t->device);
     DevState& d = t->d;
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, t->device) != cudaSuccess || d.sms < 1) {
+        cudaGetLastError();  // not sticky; the allocations below report a missing device
+        d.sms = 1;
+    }
     d.Q = (int)lattice; d.prec = (int)precision;
     d.nx = nx; d.ny = ny; d.nz = nz; d.N = N;
     d.Np = (N + 63) / 64 * 64;
@@ -295,7 +317,7 @@ tlbm_kernel tlbm_get_kernel(const tlbm* t) {
 // Tile choice of the fused step: variant (0 = default) and planes per chunk (0 = auto).
 tlbm_status tlbm_set_tile(tlbm* t, int variant, int chunk) {
     if (!t) return TLBM_ERR_ARG;
-    if (variant < 0 || variant > 255 || (variant & 15) > 3 || chunk < 0 || chunk > 4096)
+    if (variant < 0 || variant > 255 || (variant & 15) > 8 || chunk < 0 || chunk > 4096)
         return fail(t, TLBM_ERR_ARG, "bad tile");
     t->d.tile = variant + 256 * chunk;
     // partial sums must fit: blocks grow as chunks shrink
@@ -699,7 +721,7 @@ int64_t tlbm_batch_blocks(const tlbm_batch* b) { return b ? (int64_t)b->bs.block
 
 tlbm_status tlbm_batch_set_tile(tlbm_batch* b, int variant, int chunk) {
     if (!b) return TLBM_ERR_ARG;
-    if (variant < 0 || variant > 255 || (variant & 15) > 3 || chunk < 0 || chunk > 4096)
+    if (variant < 0 || variant > 255 || (variant & 15) > 8 || chunk < 0 || chunk > 4096)
         return bfail(b, TLBM_ERR_ARG, "bad tile");
     const int old = b->bs.tile;
     b->bs.tile = variant + 256 * chunk;

@@ -42,7 +42,7 @@ struct Axes {
 
 struct MGeom {
     int NA, NB, NM;       // extents along a, b, m
-    int MC;               // planes per chunk
+    int NC;               // chunks along m; chunk c holds planes [c NM / NC, (c+1) NM / NC)
     int tilesA, tilesB;   // tiles per plane
     long long rowstride;  // bytes between consecutive (b, m) rows: ncx * chunk bytes
 };
@@ -62,17 +62,41 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// FP32 load of one stored population with an L1 eviction priority:
+// POL 1 evict_last, 2 no_allocate, 3 evict_first (0: a plain load).
+template <int POL>
+__device__ __forceinline__ float ld_l1(const unsigned char* p) {
+    float v;
+    if constexpr (POL == 1) asm("ld.global.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    else if constexpr (POL == 2) asm("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    else if constexpr (POL == 3) asm("ld.global.L1::evict_first.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    else v = *reinterpret_cast<const float*>(p);
+    return v;
+}
+
 // ILP: a thread's border node loads interleave with its own node's loads.
 // EARLY: phase C's loads are issued before phase M's (values held across M).
 // PF: each warp prefetches its own 32-node chunk three planes ahead into L2.
 // HINT: 1 streams the stores out (evict-first); 2 also marks phase C's loads,
 //       the last use of those lines, evict-first.
-template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false, int HINT = 0>
+// STG: the first STG population sets (f, g, k) of a thread's own node, pulled
+//      in phase M, are kept in shared memory (stg: 2 plane slots x STG x Q x NT
+//      values) and the collision reads them from there instead of pulling
+//      them again from L2.
+// L1H (FP32 storage): phase M keeps its own-node lines in L1 (evict_last),
+//      border-node loads do not allocate in L1, and the collision's loads are
+//      their last use (evict_first).
+template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false, int HINT = 0, int STG = 0,
+          int L1H = 0>
 __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__ src, S* __restrict__ dst,
                                            const Phys<typename Store<S>::T>& P, double* __restrict__ partials,
                                            const int bid) {
     using T = typename Store<S>::T;
     using A = Axes<Q>;
+    // staging ring in dynamic shared memory (declared here so that the compiler
+    // knows the stores are shared-memory stores that cannot alias the loads)
+    extern __shared__ __align__(16) unsigned char tlbm_stage_smem[];
+    T* const stg = reinterpret_cast<T*>(tlbm_stage_smem);
     constexpr int D = Lat<Q>::D;
     constexpr int HY = (D == 3) ? 1 : 0;  // halo rows along b
     constexpr int HW = TX + 2;
@@ -92,8 +116,8 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
     const int tileB = rest % g.tilesB;
     const int chunk = rest / g.tilesB;
     const int A0 = tileA * TX, B0 = tileB * TY;
-    const int M0 = chunk * g.MC;
-    const int M1 = min(M0 + g.MC, g.NM);
+    const int M0 = (int)((long long)chunk * g.NM / g.NC);
+    const int M1 = (int)((long long)(chunk + 1) * g.NM / g.NC);
     const bool active = (A0 + tx < g.NA) && (B0 + ty < g.NB);
 
     // Node 0 of every thread: its own tile slot (coordinates wrap for threads past
@@ -134,6 +158,18 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
     const int nnodes = tid < NBORDER ? 2 : 1;
 
     const unsigned char* srcb = reinterpret_cast<const unsigned char*>(src);
+    // stored value (x - bias) of (s, i) at node pointer p; pol selects the L1
+    // policy of the L1H variant (1 own node in phase M, 2 border node, 3 collision)
+    auto ldp = [&](const unsigned char* p, int s, int i, int pol) -> T {
+        if constexpr (L1H != 0 && sizeof(S) == 4) {
+            const unsigned char* q = p + Fmt<Q, S>::off(s, i);
+            if (pol == 1) return ld_l1<1>(q);
+            if (pol == 2) return ld_l1<2>(q);
+            return ld_l1<3>(q);
+        } else {
+            return Fmt<Q, S>::ld_delta(p, s, i);
+        }
+    };
     // pull source of direction (ca, cb, cm) for node n at plane rows zr
     auto src_of = [&](int n, const int (&zr)[3], int ca, int cb, int cm) -> const unsigned char* {
         const long long row = (long long)zr[1 - cm] * g.NB + yb[n][1 - cb];
@@ -152,27 +188,35 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const unsigned char* p0 = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
-            const T f = Fmt<Q, S>::ld_delta(p0, 0, i);
+            const T f = ldp(p0, 0, i, 1);
+            const T gg = ldp(p0, 1, i, 1);
+            const T kk = ldp(p0, 2, i, 1);
             rho0 += f;
             if (A::ca(i)) ja += T(A::ca(i)) * f;
             if (A::cb(i)) jb += T(A::cb(i)) * f;
             if (A::cm(i)) jm += T(A::cm(i)) * f;
-            phi0 += Fmt<Q, S>::ld_delta(p0, 1, i);
-            psi0 += Fmt<Q, S>::ld_delta(p0, 2, i);
+            phi0 += gg;
+            psi0 += kk;
+            if constexpr (STG > 0) {
+                T* sp = stg + ((size_t)((m & 1) * STG) * Q + i) * NT + tid;
+                sp[0] = f;
+                if (STG > 1) sp[(size_t)Q * NT] = gg;
+                if (STG > 2) sp[(size_t)2 * Q * NT] = kk;
+            }
             if (ILP && two) {  // border node of this thread, loads interleaved with node 0
                 const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                rho1 += Fmt<Q, S>::ld_delta(p1, 0, i);
-                phi1 += Fmt<Q, S>::ld_delta(p1, 1, i);
-                psi1 += Fmt<Q, S>::ld_delta(p1, 2, i);
+                rho1 += ldp(p1, 0, i, 2);
+                phi1 += ldp(p1, 1, i, 2);
+                psi1 += ldp(p1, 2, i, 2);
             }
         }
         if (!ILP && two) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                rho1 += Fmt<Q, S>::ld_delta(p1, 0, i);
-                phi1 += Fmt<Q, S>::ld_delta(p1, 1, i);
-                psi1 += Fmt<Q, S>::ld_delta(p1, 2, i);
+                rho1 += ldp(p1, 0, i, 2);
+                phi1 += ldp(p1, 1, i, 2);
+                psi1 += ldp(p1, 2, i, 2);
             }
         }
         rd = rho0;
@@ -209,7 +253,12 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const unsigned char* pi = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
-                if (HINT >= 2) {
+                if constexpr (STG > 0 || L1H != 0) {
+                    const T* sp = stg + ((size_t)((m & 1) * STG) * Q + i) * NT + tid;
+                    fv[i] = (STG > 0 ? sp[0] : ldp(pi, 0, i, 3)) + T(Fmt<Q, S>::bias(0, i));
+                    gv[i] = (STG > 1 ? sp[(size_t)Q * NT] : ldp(pi, 1, i, 3)) + T(Fmt<Q, S>::bias(1, i));
+                    kv[i] = (STG > 2 ? sp[(size_t)2 * Q * NT] : ldp(pi, 2, i, 3)) + T(Fmt<Q, S>::bias(2, i));
+                } else if (HINT >= 2) {
                     fv[i] = Fmt<Q, S>::ld_last(pi, 0, i);
                     gv[i] = Fmt<Q, S>::ld_last(pi, 1, i);
                     kv[i] = Fmt<Q, S>::ld_last(pi, 2, i);
@@ -358,6 +407,15 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
     fused_body<Q, S, TX, TY, ILP, EARLY, PF, HINT>(g, src, dst, P, partials, blockIdx.x);
 }
 
+// Variants of the periodic step with shared-memory staging of the pulled
+// populations (STG sets) or L1 eviction priorities (L1H), at BPS blocks per SM.
+template <int Q, typename S, int TX, int TY, int STG, int L1H, int BPS>
+__global__ void __launch_bounds__(TX * TY, BPS)
+k_fused_x(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename Store<S>::T> P,
+          double* __restrict__ partials) {
+    fused_body<Q, S, TX, TY, false, false, false, 1, STG, L1H>(g, src, dst, P, partials, blockIdx.x);
+}
+
 // ------------------------------------------------------ solid-aware variant
 
 // Bit i (1 <= i < Q) of nbm[r]: the pull source r - e_i of node r is solid;
@@ -420,8 +478,8 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
     const int tileB = rest % g.tilesB;
     const int chunk = rest / g.tilesB;
     const int A0 = tileA * TX, B0 = tileB * TY;
-    const int M0 = chunk * g.MC;
-    const int M1 = min(M0 + g.MC, g.NM);
+    const int M0 = (int)((long long)chunk * g.NM / g.NC);
+    const int M1 = (int)((long long)(chunk + 1) * g.NM / g.NC);
     const bool active = (A0 + tx < g.NA) && (B0 + ty < g.NB);
     const long long plane = (long long)g.NA * g.NB;
 
@@ -762,12 +820,20 @@ __global__ void k_mass_final_batch(const SimDesc<T>* __restrict__ d) {
 
 // ------------------------------------------------------------ host side
 
+// grid of a grid-stride kernel of 256 threads over n items: at most 8 blocks
+// per SM (results do not depend on it)
+inline int grid_of(long long n, int sms) {
+    const long long b = (n + 255) / 256, cap = 8LL * (sms < 1 ? 1 : sms);
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
 // tile variants: 0 = default (D3Q19 32x4, D2Q9 128); D3Q19: 1 = 32x8, 2 = 64x4, 3 = 32x4;
 // D2Q9: 1 = 128, 2 = 256, 3 = 64.  tile = variant + 16 * chunk (chunk 0 = auto).
 template <int Q>
 struct FusedCfg {
     int TX, TY, MC;
     int mode;
+    int shape;  // resolved shape (D3Q19 4..8: 32x4 variants of k_fused_x)
 };
 
 // d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 32x4,
@@ -795,7 +861,8 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
     } else if (Q == 19) {
         const int v = variant == 0 ? 3 : variant;  // 32x4 measured fastest on 256^3
         c.TX = v == 2 ? 64 : 32;
-        c.TY = v == 2 ? 4 : (v == 3 ? 4 : 8);
+        c.TY = v == 1 ? 8 : 4;
+        c.shape = v;
     } else {
         const int v = variant == 0 ? 1 : variant;
         c.TX = v == 2 ? 256 : (v == 3 ? 64 : 128);
@@ -812,10 +879,10 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
     const int NB = (Q == 19) ? d.ny : 1;
     const int NM = (Q == 19) ? d.nz : d.ny;
     if (mc <= 0) {
-        // enough blocks to fill 152 SMs a few times over
+        // enough blocks to fill every SM of the device a few times over
         const long long cols = (long long)((NA + c.TX - 1) / c.TX) * ((NB + c.TY - 1) / c.TY);
         mc = (Q == 19) ? 16 : 64;
-        while (mc > 4 && cols * ((NM + mc - 1) / mc) < 4 * 152) mc >>= 1;
+        while (mc > 4 && cols * ((NM + mc - 1) / mc) < 4LL * d.sms) mc >>= 1;
     }
     c.MC = mc < 1 ? 1 : (mc > NM ? NM : mc);
     return c;
@@ -838,7 +905,7 @@ inline MGeom mgeom(const tlbm_host::DevState& d, const FusedCfg<Q>& c) {
     g.NB = (Q == 19) ? d.ny : 1;
     g.NM = (Q == 19) ? d.nz : d.ny;
     g.rowstride = (long long)d.ncx * Fmt<Q, S>::CHUNK;
-    g.MC = c.MC;
+    g.NC = (g.NM + c.MC - 1) / c.MC;  // chunks of MC planes or one fewer (balanced)
     g.tilesA = (g.NA + c.TX - 1) / c.TX;
     g.tilesB = (g.NB + c.TY - 1) / c.TY;
     return g;
@@ -848,7 +915,7 @@ template <int Q, typename S>
 inline long long fused_blocks(const tlbm_host::DevState& d) {
     const FusedCfg<Q> c = fused_cfg<Q>(d);
     const MGeom g = mgeom<Q, S>(d, c);
-    return (long long)g.tilesA * g.tilesB * ((g.NM + g.MC - 1) / g.MC);
+    return (long long)g.tilesA * g.tilesB * g.NC;
 }
 
 // number of partial sums the last step wrote (for k_mass_final)
@@ -861,14 +928,14 @@ template <int Q, typename S>
 inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<S>::T>& P, cudaStream_t st) {
     const FusedCfg<Q> c = fused_cfg<Q>(d);
     const MGeom g = mgeom<Q, S>(d, c);
-    const long long nb = (long long)g.tilesA * g.tilesB * ((g.NM + g.MC - 1) / g.MC);
+    const long long nb = (long long)g.tilesA * g.tilesB * g.NC;
     if (nb > 0x7fffffffLL || nb > d.partials_cap) return cudaErrorInvalidConfiguration;
     const S* src = static_cast<const S*>(d.pop[d.cur]);
     S* dst = static_cast<S*>(d.pop[1 - d.cur]);
     if (d.solid) {
         if (!d.nbm_ready) {
             const Geom gg{d.nx, d.ny, d.nz, d.N, d.Np, d.ncx};
-            k_nbmask<Q><<<1216, 256, 0, st>>>(gg, d.solid, d.nbm);
+            k_nbmask<Q><<<grid_of(d.N, d.sms), 256, 0, st>>>(gg, d.solid, d.nbm);
             d.nbm_ready = 1;
         }
         auto gos = [&](auto kern, int threads) {
@@ -890,6 +957,29 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
         if constexpr (Q == 19) go(k_fused<Q, S, 16, 8, false, false>, 128);
         else go(k_fused<Q, S, 128, 1, false, false>, 128);
     } else if constexpr (Q == 19) {
+        if constexpr (sizeof(S) == 4) {
+            if (c.shape >= 4) {
+                // 32x4 variants: 4 all sets staged in shared memory, 3 blocks/SM; 5 f and g
+                // staged, 4 blocks/SM; 6 / 7 L1 eviction priorities at 4 / 3 blocks/SM;
+                // 8 the default loop at 3 blocks/SM
+                auto gox = [&](auto kern, int stg, int bps) {
+                    const int dyn = stg * 2 * Q * 128 * (int)sizeof(float);
+                    const int ring = 4 * 3 * 34 * 6 * (int)sizeof(float);
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+                    const int pct = (bps * (dyn + ring + 1024) * 100 + 233471) / 233472;
+                    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
+                    kern<<<(int)nb, 128, dyn, st>>>(g, src, dst, P, d.partials);
+                };
+                switch (c.shape) {
+                    case 4: gox(k_fused_x<Q, S, 32, 4, 3, 0, 3>, 3, 3); break;
+                    case 5: gox(k_fused_x<Q, S, 32, 4, 2, 0, 4>, 2, 4); break;
+                    case 6: gox(k_fused_x<Q, S, 32, 4, 1, 0, 4>, 1, 4); break;
+                    case 7: gox(k_fused_x<Q, S, 32, 4, 0, 1, 3>, 0, 3); break;
+                    default: gox(k_fused_x<Q, S, 32, 4, 0, 0, 3>, 0, 3);
+                }
+                return cudaGetLastError();
+            }
+        }
         if (c.TX == 64) {
             switch (c.mode) {
                 case 2: go(k_fused<Q, S, 64, 4, false, true>, 256); break;
@@ -950,7 +1040,7 @@ inline cudaError_t batch_build(tlbm_host::BatchState& b, cudaStream_t st) {
         if ((d.solid != nullptr) != solid || d.cur != b.sims[0]->cur) return cudaErrorInvalidValue;
         if (solid && !d.nbm_ready) {
             const Geom gg{d.nx, d.ny, d.nz, d.N, d.Np, d.ncx};
-            k_nbmask<Q><<<1216, 256, 0, st>>>(gg, d.solid, d.nbm);
+            k_nbmask<Q><<<grid_of(d.N, d.sms), 256, 0, st>>>(gg, d.solid, d.nbm);
             d.nbm_ready = 1;
         }
         tlbm_host::DevState dd = d;
@@ -962,7 +1052,7 @@ inline cudaError_t batch_build(tlbm_host::BatchState& b, cudaStream_t st) {
                                                 : c.TX == 128);
         if (!shape_ok) return cudaErrorInvalidConfiguration;
         const MGeom g = mgeom<Q, S>(dd, c);
-        const long long nb = (long long)g.tilesA * g.tilesB * ((g.NM + g.MC - 1) / g.MC);
+        const long long nb = (long long)g.tilesA * g.tilesB * g.NC;
         if (nb > d.partials_cap) return cudaErrorInvalidConfiguration;
         for (int par = 0; par < 2; ++par) {
             SimDesc<T>& e = h[(size_t)par * n + k];

@@ -17,6 +17,18 @@ struct PhysD {
     double K[3][3];   // mixing coefficients kappa_XY
 };
 
+// Blocks of the fixed grid of the split step's moment/mass kernels and of
+// tlbm_mass.  Fixed (not derived from the device) so that the FP64 totals are
+// summed in the same order, hence bitwise the same, on every GPU.
+constexpr int kMassBlocks = 1216;
+
+// Physical parameters of the step from the ABI's arguments (Gamma_phi,
+// Gamma_psi = 1 unless set): relaxation rates, wall-normal gradients of the
+// wetting condition and the pressure tensor's mixing coefficients.  One helper
+// for the engine and the allocation-free step.
+PhysD make_phys(const double kappa[3], double alpha, double tau_f, double M_phi, double M_psi,
+                const double gamma[2], const double h[3]);
+
 enum Kind { KIND_FUSED = 1, KIND_SPLIT = 2 };
 
 struct DevState {
@@ -38,6 +50,7 @@ struct DevState {
     int* flag;           // non-finite flag (int)
     PhysD phys;
     int tile;            // fused-kernel tile choice (0 = default)
+    int sms;             // multiprocessors of the device (sizes the fused grid's chunks)
     long long partials_cap;  // blocks whose partial sums fit in the first part of partials
 };
 
@@ -93,11 +106,18 @@ struct Ops {
     cudaError_t (*adjoint)(DevState& d, int kind, const AdjJob& job, cudaStream_t st);
 };
 
-// one table per storage format; nullptr if the lattice is not built
-const Ops* ops_fp64(int Q);
-const Ops* ops_fp32(int Q);
-const Ops* ops_fp16(int Q);
-const Ops* ops_bf16(int Q);
+// one table per storage format and lattice (one translation unit each)
+const Ops* ops_fp64_q9();
+const Ops* ops_fp64_q19();
+const Ops* ops_fp32_q9();
+const Ops* ops_fp32_q19();
+const Ops* ops_fp16_q9();
+const Ops* ops_fp16_q19();
+const Ops* ops_bf16_q9();
+const Ops* ops_bf16_q19();
+
+// the table of a storage format (tlbm_precision) and lattice (Q); nullptr if not built
+const Ops* ops_for(int precision, int Q);
 
 int mass_blocks();
 

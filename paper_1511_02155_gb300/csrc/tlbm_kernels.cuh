@@ -37,7 +37,7 @@ inline Phys<T> to_phys(const tlbm_host::PhysD& p) {
     return q;
 }
 
-constexpr int kMassBlocks = 1216;  // 8 x 152 SMs; fixed so reductions are repeatable
+constexpr int kMassBlocks = tlbm_host::kMassBlocks;  // fixed so reductions are repeatable
 
 // ------------------------------------------------------------ small helpers
 

@@ -13,9 +13,11 @@ using tlbm_host::PhysD;
 
 inline Geom geom(const DevState& d) { return Geom{d.nx, d.ny, d.nz, d.N, d.Np, d.ncx}; }
 
-inline int grid_for(long long n) {
+// grid of a grid-stride kernel over n items: at most 8 blocks per SM (the
+// results do not depend on the grid)
+inline int grid_for(long long n, int sms) {
     long long b = (n + kThreads - 1) / kThreads;
-    const long long cap = 152LL * 8;
+    const long long cap = 8LL * (sms < 1 ? 1 : sms);
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
@@ -30,7 +32,7 @@ struct Impl {
         const S* src = static_cast<const S*>(d.pop[d.cur]);
         S* dst = static_cast<S*>(d.pop[1 - d.cur]);
         T* mom = static_cast<T*>(d.mom);
-        const int grid = grid_for(g.N);
+        const int grid = grid_for(g.N, d.sms);
         k_moments<Q, S, SOLID, true><<<kMassBlocks, kThreads, 0, st>>>(g, src, d.solid, mom, d.partials);
         if (SOLID) k_ghosts<Q, T><<<grid, kThreads, 0, st>>>(g, d.solid, mom, P);
         k_collide_split<Q, S, SOLID><<<grid, kThreads, 0, st>>>(g, src, dst, d.solid, mom, P);
@@ -58,7 +60,7 @@ struct Impl {
         const Phys<T> P = to_phys<T>(d.phys);
         T* mom = static_cast<T*>(d.mom);
         S* dst = static_cast<S*>(d.pop[d.cur]);
-        const int grid = grid_for(g.N);
+        const int grid = grid_for(g.N, d.sms);
         k_fields_to_mom<T><<<grid, kThreads, 0, st>>>(g, rho, phi, psi, d.solid, mom);
         if (d.solid) {
             k_ghosts<Q, T><<<grid, kThreads, 0, st>>>(g, d.solid, mom, P);
@@ -73,7 +75,7 @@ struct Impl {
                               cudaStream_t st) {
         const Geom g = geom(d);
         const S* src = static_cast<const S*>(d.pop[d.cur]);
-        const int grid = grid_for(g.N);
+        const int grid = grid_for(g.N, d.sms);
         if (d.solid) k_fields<Q, S, true><<<grid, kThreads, 0, st>>>(g, src, d.solid, C1, C2, C3, rho, u);
         else k_fields<Q, S, false><<<grid, kThreads, 0, st>>>(g, src, d.solid, C1, C2, C3, rho, u);
         return cudaGetLastError();
@@ -95,7 +97,7 @@ struct Impl {
                                cudaStream_t st) {
         const Geom g = geom(d);
         const S* src = static_cast<const S*>(d.pop[d.cur]);
-        const int grid = grid_for((long long)bx * by * bz);
+        const int grid = grid_for((long long)bx * by * bz, d.sms);
         if (d.solid)
             k_get_box<Q, S, true><<<grid, kThreads, 0, st>>>(g, src, d.solid, x0, y0, z0, bx, by, bz, out);
         else
@@ -106,7 +108,7 @@ struct Impl {
     static cudaError_t set_pops(DevState& d, const double* in, cudaStream_t st) {
         const Geom g = geom(d);
         S* dst = static_cast<S*>(d.pop[d.cur]);
-        const int grid = grid_for(g.N);
+        const int grid = grid_for(g.N, d.sms);
         if (d.solid) k_set_pops<Q, S, true><<<grid, kThreads, 0, st>>>(g, in, d.solid, dst);
         else k_set_pops<Q, S, false><<<grid, kThreads, 0, st>>>(g, in, d.solid, dst);
         return cudaGetLastError();
@@ -124,7 +126,7 @@ struct Impl {
         const Geom g = geom(d);
         const Phys<T> P = to_phys<T>(d.phys);
         T* mom = static_cast<T*>(d.mom);
-        const int grid = grid_for(g.N);
+        const int grid = grid_for(g.N, d.sms);
         const long long Np = g.Np;
         T* wk = reinterpret_cast<T*>(J.work);
         T *dX = wk, *dJ = wk + 3 * Np, *dG = wk + 6 * Np, *dL = wk + 15 * Np;
@@ -221,11 +223,8 @@ struct Impl {
 
 }  // namespace tlbm_dev
 
-#define TLBM_DEFINE_OPS(NAME, S)                                   \
+// the launch table of storage type S on lattice Q, as tlbm_host::NAME()
+#define TLBM_DEFINE_OPS(NAME, S, Q)                                \
     namespace tlbm_host {                                          \
-    const Ops* NAME(int Q) {                                       \
-        if (Q == 9) return tlbm_dev::Impl<9, S>::table();          \
-        if (Q == 19) return tlbm_dev::Impl<19, S>::table();        \
-        return nullptr;                                            \
-    }                                                              \
+    const Ops* NAME() { return tlbm_dev::Impl<Q, S>::table(); }    \
     }

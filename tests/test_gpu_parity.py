@@ -296,7 +296,7 @@ def test_tile_variants_are_bitwise_identical():
     n = 40
     C = W.spinodal((n, n, n), seed=8, amp=0.05)
     ref = None
-    for variant, chunk in ((0, 0), (1, 8), (2, 3), (3, 40), (1, 1)):
+    for variant, chunk in ((0, 0), (1, 8), (2, 3), (3, 40), (1, 1), (4, 0), (5, 7), (6, 0), (7, 13), (8, 6)):
         eng = tl.TernaryLB(19, n, n, n, (0.01, 0.01, 0.01), 1.0, 0.8, 0.1, 0.1, precision="fp32")
         eng.set_tile(variant, chunk)
         eng.init_fields(*W.to_aux(*C))
