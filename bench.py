@@ -8,6 +8,9 @@ streaming, FP64 mass totals).  Metric: million lattice-node updates per second
 
 Default workload: D3Q19 256^3 periodic ternary spinodal decomposition (FP32),
 populations 3.8 GB per copy (larger than L2, so every step streams from HBM).
+The default run also times the FP16 and BF16 storage formats on the same
+lattice and reports them under "companions" (MLUPS, kernel time, roofline
+fractions, largest |dC_m| against the FP32 run after the same steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload spinodal256|lens512|probe8192] [--precision fp32|fp64|fp16|bf16]
@@ -426,6 +429,8 @@ def main():
     ap.add_argument("--tile", default="0,0")
     ap.add_argument("--size", type=int, default=0, help="lattice edge override (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-companions", action="store_true",
+                    help="skip the FP16/BF16 storage companions of the default FP32 run")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -463,20 +468,106 @@ def main():
     if solid is not None:
         for a in (rho, phi, psi):
             a[solid != 0] = 0.0
-    eng = tl.TernaryLB(Q, nx, ny, nz, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"],
-                       cfg["M_psi"], cfg["h"], solid, args.precision)
-    if args.kernel != "auto":
-        eng.set_kernel(args.kernel)
-    tv, tc = (int(v) for v in args.tile.split(","))
-    eng.set_tile(tv, tc)
-    eng.init_fields(rho, phi, psi)
-    stream = torch.cuda.current_stream()
+    n_fluid = N if solid is None else int(N - np.count_nonzero(solid))
+    fields = (rho, phi, psi)
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+
+    with_companions = (args.precision == "fp32" and args.workload == "spinodal256" and not args.no_companions)
+    main_run = measure(args, cfg, fields, solid, args.precision, args.tile, args.kernel, world, local, dist,
+                       barrier, keep_fields=with_companions)
+    value, ms, clocks, m_after = main_run["value"], main_run["ms"], main_run["clocks"], main_run["mass"]
+    kernel_ms, kind, e2e, launches = (main_run["kernel_ms"], main_run["kind"], main_run["e2e"],
+                                      main_run["launches"])
+    bpn = bytes_per_node(Q, args.precision)
+    # every population of a fluid node read once and written once, plus one mask
+    # byte per node where solid nodes exist
+    alg_bytes = bpn * n_fluid + (0 if solid is None else N)
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    tag = f"{kind}:{args.workload}:{args.precision}:{args.tile}"
+    traffic = traffic_from_profiles(tag, kernel_source_digest(), N)
+
+    # the 16-bit storage companions of the FP32 headline (the metric compares
+    # FP32 and FP16 storage): same lattice and timing; roofline fractions against
+    # 228 B/node (every population in 16 bits) and against the 240 B/node the
+    # packed format stores (rest populations in FP32); the largest |dC_m|
+    # against the FP32 run after the same steps from the same fields
+    companions = None
+    if with_companions:
+        companions = {}
+        for prec in ("fp16", "bf16"):
+            c = measure(args, cfg, fields, solid, prec, "0,0", "auto", world, local, dist, barrier,
+                        keep_fields=True)
+            dC = max(float(np.abs(a - b).max()) for a, b in zip(c["C"], main_run["C"]))
+            b228, b240 = 2 * 3 * Q * 2, bytes_per_node(Q, prec)
+            companions[prec] = {
+                "value": round(c["value"], 2), "unit": "MLUPS",
+                "ms_per_step": round(c["ms"] / args.steps, 4), "kernel_ms": round(c["kernel_ms"], 4),
+                "frac_228": round(b228 * n_fluid / (c["kernel_ms"] / 1e3) / 1e9 / peak, 4),
+                "frac_240": round(b240 * n_fluid / (c["kernel_ms"] / 1e3) / 1e9 / peak, 4),
+                "e2e_mlups": c["e2e"]["value"], "clocks": c["clocks"],
+                "max_dC_vs_fp32": dC, "steps_compared": args.steps,
+            }
+        main_run.pop("C", None)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-store/f32",
+                                           "bf16": "bf16-store/f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": label, "nodes_per_gpu": N, "fluid_nodes_per_gpu": n_fluid,
+                       "lattice": f"D{3 if Q == 19 else 2}Q{Q}",
+                       "precision": args.precision, "kernel": kind,
+                       "l2": "populations exceed L2 (no flush needed)" if alg_bytes / 2 > 129e6
+                       else "L2-resident lattice", "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+                         "kernel_ms": round(kernel_ms, 4),
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "bytes_per_node": bpn},
+            "e2e": e2e,
+            "gpu_launches": args.steps * launches,
+            "clocks": clocks,
+            "mass_totals": [float(v) for v in m_after],
+        }
+        if companions:
+            line["companions"] = companions
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.workload, cfg)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def measure(args, cfg, fields, solid, precision, tile, kernel, world, local, dist, barrier, keep_fields=False):
+    """Time one engine of the workload in one storage format: W warm-up steps,
+    K timed steps (CUDA events on the engine's stream, clocks sampled), the main
+    kernel's own duration in timing mode, and the end-to-end job through the
+    public API with host buffers.  keep_fields: also return the end-to-end job's
+    C_1..3 (host arrays)."""
+    import torch
+    import paper_1511_02155_gb300 as tl
+    Q = cfg["Q"]
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    N = nx * ny * nz
+    rho, phi, psi = fields
+    eng = tl.TernaryLB(Q, nx, ny, nz, cfg["kappa"], cfg["alpha"], cfg["tau_f"], cfg["M_phi"],
+                       cfg["M_psi"], cfg["h"], solid, precision)
+    if kernel != "auto":
+        eng.set_kernel(kernel)
+    tv, tc = (int(v) for v in tile.split(","))
+    eng.set_tile(tv, tc)
+    eng.init_fields(rho, phi, psi)
+    stream = torch.cuda.current_stream()
 
     # warm-up
     eng.step(args.warmup)
@@ -502,16 +593,6 @@ def main():
     kms, ksteps = eng.kernel_time()
     eng.set_timing(False)
     kernel_ms = kms / max(ksteps, 1)
-    bpn = bytes_per_node(Q, args.precision)
-    n_fluid = N if solid is None else int(N - np.count_nonzero(solid))
-    # every population of a fluid node read once and written once, plus one mask
-    # byte per node where solid nodes exist
-    alg_bytes = bpn * n_fluid + (0 if solid is None else N)
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    kind = eng.kernel
-    tag = f"{kind}:{args.workload}:{args.precision}:{args.tile}"
-    traffic = traffic_from_profiles(tag, kernel_source_digest(), N)
 
     # end to end through the public API with host buffers: upload the fields from
     # pinned memory, K steps, download C_1..3 and the mass totals
@@ -530,37 +611,12 @@ def main():
            "d2h_bytes_per_step": round((3 * 8 * N + 24) / args.steps, 1),
            "job": f"upload rho/phi/psi (fp64, pinned) + equilibrium init, {args.steps} steps, "
                   "download C1..C3 (fp64) + mass totals"}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "fp16": "f16-store/f32",
-                                           "bf16": "bf16-store/f32"}[args.precision],
-            "data": "synthetic",
-            "config": {"workload": label, "nodes_per_gpu": N, "fluid_nodes_per_gpu": n_fluid,
-                       "lattice": f"D{3 if Q == 19 else 2}Q{Q}",
-                       "precision": args.precision, "kernel": kind,
-                       "l2": "populations exceed L2 (no flush needed)" if alg_bytes / 2 > 129e6
-                       else "L2-resident lattice", "parallelism": f"replicas x{world}"},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
-                         "kernel_ms": round(kernel_ms, 4),
-                         "algorithmic_bytes_per_launch": alg_bytes,
-                         "bytes_per_node": bpn},
-            "e2e": e2e,
-            "gpu_launches": args.steps * eng.launches_per_step,
-            "clocks": clocks,
-            "mass_totals": [float(v) for v in m_after],
-        }
-        if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.workload, cfg)
-        print(json.dumps(line), flush=True)
+    out = {"value": value, "ms": ms, "clocks": clocks, "mass": m_after, "kernel_ms": kernel_ms,
+           "kind": eng.kernel, "e2e": e2e, "launches": eng.launches_per_step}
     eng.close()
-    if dist is not None:
-        dist.destroy_process_group()
+    if keep_fields:
+        out["C"] = [t.numpy() for t in outs]
+    return out
 
 
 if __name__ == "__main__":

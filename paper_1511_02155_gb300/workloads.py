@@ -173,14 +173,18 @@ def sessile_drop(nx: int, ny: int, R: float, m: int = 2, n: int = 0, alpha: floa
 
 
 def square_well(nx: int, ny: int, width: int, depth: int, floor: int = 8, alpha: float = 1.0,
-                drop_radius=None):
+                drop_radius=None, fill: float = 1.0, info: bool = False):
     """Square-well geometry of the contact-angle benchmark (Sec. Contact Angles).
 
     Solid: the bottom ``floor`` rows plus the top row, with a well of the given
     width and depth cut into a solid block that rises ``depth`` above the floor.
-    The well is filled with fluid 3; fluid 1 lies below a flat 1/2 interface at
-    mid-height of the open region, fluid 2 above it.
-    Returns ([C1, C2, C3], solid) with arrays of shape [ny][nx].
+    The well is filled with fluid 3 up to ``fill`` of its depth (a flat surface
+    with a tanh edge); fluid 1 fills the rest of the open region below a flat
+    1/2 interface at mid-height of the region above the block, fluid 2 lies
+    above it.  Returns ([C1, C2, C3], solid) with arrays of shape [ny][nx], and
+    with info=True also the well's extent {x0, x1, y0, y1}: fluid columns
+    x0..x1-1 between walls at x0 - 1/2 and x1 - 1/2, floor at y0 - 1/2, top of
+    the block at y1 - 1/2.
     """
     solid = np.zeros((ny, nx), dtype=np.uint8)
     top_of_block = min(floor + depth, ny - 4)
@@ -191,8 +195,9 @@ def square_well(nx: int, ny: int, width: int, depth: int, floor: int = 8, alpha:
     solid[ny - 1, :] = 1
     x, y = _grid2(nx, ny)
     # well filled with fluid 3 (a rectangle with diffuse top edge)
+    level = floor - 0.5 + fill * (top_of_block - floor)
     inwell = (x >= x0) & (x < x1) & (y < top_of_block)
-    C3 = np.where(inwell, profile(top_of_block - 0.5 - y, alpha), 0.0)
+    C3 = np.where(inwell, profile(level - y, alpha), 0.0)
     if drop_radius is not None:
         r = np.hypot(x - nx / 2, y - top_of_block)
         C3 = np.maximum(C3, profile(-(r - drop_radius), alpha))
@@ -202,6 +207,8 @@ def square_well(nx: int, ny: int, width: int, depth: int, floor: int = 8, alpha:
     C2 = (1 - C3) * (1 - B)
     for c in (C1, C2, C3):
         c[solid != 0] = 0.0
+    if info:
+        return [C1, C2, C3], solid, dict(x0=x0, x1=x1, y0=floor, y1=top_of_block)
     return [C1, C2, C3], solid
 
 
@@ -292,10 +299,13 @@ def sweep_wells(count: int = 96, seed: int = 7, ncand: int = 16):
 
     Member k: nx = 128 + 32 j, j uniform in {0..20}, ny = nx / 2; floor 8 rows,
     a well of width uniform in [20, 120] (at most nx - 16) and depth uniform in
-    [10, 60] (clipped to the lattice), filled with fluid 3, fluid 1 below a flat
-    1/2 interface and fluid 2 above.  ``angles`` holds ``ncand`` candidate
-    target pairs (theta_12, theta_13) uniform in [30, 150) degrees; the caller
-    keeps the first pair its wetting inversion accepts and sets ``h`` from it.
+    [10, 60] (clipped to the lattice), its lower half filled with fluid 3 (the
+    fluid-3/fluid-1 meniscus meets the well's side walls, away from its
+    corners), fluid 1 above it and below a flat 1/2 interface, fluid 2 above.
+    ``angles`` holds ``ncand`` candidate target pairs (theta_12, theta_13)
+    uniform in [30, 150) degrees; the caller keeps the first pair its wetting
+    inversion accepts and sets ``h`` from it.  ``well`` is the well's extent
+    (square_well's info).
     """
     out = []
     for k in range(count):
@@ -304,8 +314,8 @@ def sweep_wells(count: int = 96, seed: int = 7, ncand: int = 16):
         ny = nx // 2
         width = min(int(20 + 100 * u[1]), nx - 16)
         depth = int(10 + 50 * u[2])
-        C, solid = square_well(nx, ny, width, depth, floor=8)
+        C, solid, well = square_well(nx, ny, width, depth, floor=8, fill=0.5, info=True)
         angles = [(30 + 120 * u[3 + 2 * j], 30 + 120 * u[4 + 2 * j]) for j in range(ncand)]
         out.append(dict(Q=9, nx=nx, ny=ny, nz=1, kappa=(0.01, 0.01, 0.01), alpha=1.0, tau_f=1.0,
-                        M_phi=0.5, M_psi=1.0 / 6.0, h=None, C=C, solid=solid, angles=angles))
+                        M_phi=0.5, M_psi=1.0 / 6.0, h=None, C=C, solid=solid, angles=angles, well=well))
     return out

@@ -83,3 +83,33 @@ def test_every_sweep_member_has_an_admissible_target():
             ok = True
             break
         assert ok
+
+
+@pytest.mark.parametrize("theta", [20.0, 45.0, 80.0, 90.0, 100.0, 135.0, 160.0])
+def test_meniscus_angle_reads_synthetic_arcs(theta):
+    """The well-meniscus reader recovers the contact angle of an exact circular
+    meniscus (tanh profile of width 1 across it) to 0.3 degrees, and reports
+    whether the contact line is free or at a corner."""
+    from well_angle import meniscus_angle
+    nx, ny = 120, 90
+    well = dict(x0=30, x1=90, y0=10, y1=70)
+    a = (well["x1"] - well["x0"]) / 2.0
+    xm = well["x0"] - 0.5 + a
+    yc_line = 40.0  # contact-line height on both walls
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    if abs(theta - 90.0) < 1e-9:
+        d = y - yc_line  # signed distance above the flat meniscus
+    else:
+        R = a / abs(np.cos(np.radians(theta)))
+        # centre above the contact line when fluid 3 (below) wets (theta < 90)
+        yc = yc_line + np.sign(90.0 - theta) * np.sqrt(R * R - a * a)
+        rr = np.hypot(x - xm, y - yc)
+        d = (R - rr) if theta < 90 else (rr - R)
+    C3 = 0.5 * (1 - np.tanh(d / 2.0))
+    got, heights, free = meniscus_angle(C3, well)
+    assert got == pytest.approx(theta, abs=0.3)
+    assert free
+    assert heights[0] == pytest.approx(yc_line, abs=0.3) and heights[1] == pytest.approx(yc_line, abs=0.3)
+    # the same meniscus with its contact line at the top corner is reported pinned
+    pinned_well = dict(well, y1=int(yc_line + 1))
+    assert not meniscus_angle(C3, pinned_well)[2]
