@@ -122,14 +122,18 @@ tlbm_status tlbm_set_kernel(tlbm *t, tlbm_kernel kind);
 tlbm_kernel tlbm_get_kernel(const tlbm *t);
 
 /* Tile of the fused step.  variant = shape | mode << 4: shape 0 = default
- * (D3Q19 32x4, D2Q9 128 nodes), D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4 nodes
- * per block; D2Q9 1 = 128, 2 = 256, 3 = 64 nodes per row.  mode selects the
+ * (D3Q19 shape 5, D2Q9 128 nodes), D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4 nodes
+ * per block, 4..6 = 32x4 with part of each node's pulled populations kept in
+ * shared memory from the moment pass to the collision (4: the 19 f values;
+ * 5: the lane-shifted values first, 28 for FP32, 19 plus a per-warp L2
+ * prefetch for the 16-bit formats; 6: 19 lane-shifted values); D2Q9 1 = 128,
+ * 2 = 256, 3 = 64 nodes per row.  mode (D3Q19 shapes 1..3, D2Q9) selects the
  * load order and cache hints inside a plane (0 default for the lattice and
  * storage; 1 interleaved halo loads; 2 collision operands loaded first; 3 both;
  * 4 per-warp L2 prefetch three planes ahead; 5 = 1 + 4; 6 plain order;
  * 8 evict-first stores; 9 also evict-first collision loads; 12, 13 = 8, 9 with
  * the prefetch; a mode not built for a shape falls back to its default; the
- * variant must be below 256).
+ * variant must be below 256, its shape below 7).
  * chunk = planes marched per block (0 = chosen from the lattice size).  Double
  * storage ignores the choice.  Results do not depend on the tile. */
 tlbm_status tlbm_set_tile(tlbm *t, int variant, int chunk);
@@ -350,6 +354,24 @@ const char *tlbm_batch_last_error(const tlbm_batch *b);
 
 /* Release the batch (not its members). */
 void tlbm_batch_destroy(tlbm_batch *b);
+
+/*
+ * Bounds-checked step (a debugging aid; the paper has no counterpart).  With
+ * on != 0 the fused step of an engine with TLBM_FP32 storage runs checked
+ * variants of its default kernels: every population address of a pull, a
+ * bounce-back and a store is validated against the population buffer and its
+ * 32-node chunk layout, and every index into the on-chip moment ring and the
+ * neighbour mask against its extent.  The first violation is recorded in a
+ * device word as (code << 56 | offending offset or index), codes 1 pull
+ * source, 2 bounce-back source, 3 store target, 4 moment-ring index, 5 mask
+ * index; the access is redirected to a valid address and the kernel carries on
+ * (no trap, no fault).  The checked kernels use the default tile and compute
+ * the same results as the unchecked ones.  TLBM_ERR_UNSUPPORTED for other
+ * storage formats.  tlbm_bounds_check_word waits for the engine's stream,
+ * returns the word (0: no violation) and clears it.
+ */
+tlbm_status tlbm_set_bounds_check(tlbm *t, int on);
+tlbm_status tlbm_bounds_check_word(tlbm *t, uint64_t *word);
 
 /* Message of the last failed tlbm_step_noalloc call on this host thread ("" if none). */
 const char *tlbm_noalloc_last_error(void);

@@ -65,6 +65,8 @@ def _declare(lib):
         "tlbm_set_kernel": (i, [_H, i]),
         "tlbm_get_kernel": (i, [_H]),
         "tlbm_set_tile": (i, [_H, i, i]),
+        "tlbm_set_bounds_check": (i, [_H, i]),
+        "tlbm_bounds_check_word": (i, [_H, ctypes.POINTER(ctypes.c_uint64)]),
         "tlbm_init_fields": (i, [_H, _dp, _dp, _dp, _dp, _dp, _dp]),
         "tlbm_step": (i, [_H, i64]),
         "tlbm_steps_done": (i64, [_H]),
@@ -211,6 +213,16 @@ class TernaryLB:
     @property
     def launches_per_step(self):
         return int(self._lib.tlbm_launches_per_step(self._h))
+
+    def set_bounds_check(self, on=True):
+        """Run the bounds-checked variants of the fused step (FP32 storage)."""
+        self._check(self._lib.tlbm_set_bounds_check(self._h, 1 if on else 0))
+
+    def bounds_check_word(self):
+        """First bounds violation since the last call (code << 56 | offset), 0 if none."""
+        w = ctypes.c_uint64(0)
+        self._check(self._lib.tlbm_bounds_check_word(self._h, ctypes.byref(w)))
+        return int(w.value)
 
     def set_timing(self, on=True):
         """Time the main kernel(s) of each step with CUDA events (synchronous steps)."""

@@ -224,7 +224,7 @@ k_adj_seed(Geom g, const S* __restrict__ x, const uint8_t* __restrict__ solid, c
 #pragma unroll
             for (int s = 0; s < 3; ++s)
 #pragma unroll
-                for (int i = 0; i < Q; ++i) pst<Q, S>(lam, g, s, i, xx, yy, zz, T(0));
+                for (int i = 0; i < Q; ++i) pst_raw<Q, S>(lam, g, s, i, xx, yy, zz, T(0));
             continue;
         }
         T psi = T(0);
@@ -236,9 +236,9 @@ k_adj_seed(Geom g, const S* __restrict__ x, const uint8_t* __restrict__ solid, c
         for (int i = 0; i < Q; ++i) {
             int xs, ys, zs, is;
             pull_slot<Q, SOLID>(g, solid, i, xx, yy, zz, xs, ys, zs, is);
-            pst<Q, S>(lam, g, 0, is, xs, ys, zs, T(0));
-            pst<Q, S>(lam, g, 1, is, xs, ys, zs, T(0));
-            pst<Q, S>(lam, g, 2, is, xs, ys, zs, T(2.0 * d));
+            pst_raw<Q, S>(lam, g, 0, is, xs, ys, zs, T(0));
+            pst_raw<Q, S>(lam, g, 1, is, xs, ys, zs, T(0));
+            pst_raw<Q, S>(lam, g, 2, is, xs, ys, zs, T(2.0 * d));
         }
     }
     double z1 = 0.0, z2 = 0.0;
@@ -298,6 +298,7 @@ k_adj_node(Geom g, const S* __restrict__ x, const uint8_t* __restrict__ solid,
                 X[1] += pull_delta<Q, S, SOLID>(g, x, solid, 1, i, xx, yy, zz);
                 X[2] += pull_delta<Q, S, SOLID>(g, x, solid, 2, i, xx, yy, zz);
             }
+            if (Fmt<Q, S>::OFFSET) X[0] += T(1);  // stored f deviations sum to rho - 1
             om[0] = P.omega[0];
             om[1] = P.omega[1];
             om[2] = P.omega[2];
@@ -407,7 +408,7 @@ k_adj_pull(Geom g, const uint8_t* __restrict__ solid, const typename Store<S>::T
 #pragma unroll
                 for (int s = 0; s < 3; ++s)
 #pragma unroll
-                    for (int i = 0; i < Q; ++i) pst<Q, S>(lam_out, g, s, i, xx, yy, zz, T(0));
+                    for (int i = 0; i < Q; ++i) pst_raw<Q, S>(lam_out, g, s, i, xx, yy, zz, T(0));
             }
             continue;
         }
@@ -447,9 +448,9 @@ k_adj_pull(Geom g, const uint8_t* __restrict__ solid, const typename Store<S>::T
             const T vk = (T(1) - P.omega[2]) * Fmt<Q, S>::ld_delta(lb, 2, i) + d[2];
             int xs, ys, zs, is;
             pull_slot<Q, SOLID>(g, solid, i, xx, yy, zz, xs, ys, zs, is);
-            pst<Q, S>(lam_out, g, 0, is, xs, ys, zs, vf);
-            pst<Q, S>(lam_out, g, 1, is, xs, ys, zs, vg);
-            pst<Q, S>(lam_out, g, 2, is, xs, ys, zs, vk);
+            pst_raw<Q, S>(lam_out, g, 0, is, xs, ys, zs, vf);
+            pst_raw<Q, S>(lam_out, g, 1, is, xs, ys, zs, vg);
+            pst_raw<Q, S>(lam_out, g, 2, is, xs, ys, zs, vk);
         }
     }
 }

@@ -57,7 +57,9 @@ tlbm_status fail(tlbm* t, tlbm_status s, const char* fmt, ...) {
                         "%s failed: %s", #call, cudaGetErrorString(e_));                      \
     } while (0)
 
-void set_phys(tlbm* t) { t->d.phys = tlbm_host::make_phys(t->kappa, t->alpha, t->tau_f, t->M_phi, t->M_psi, t->gamma, t->h); }
+void set_phys(tlbm* t) {
+    t->d.phys = tlbm_host::make_phys(t->kappa, t->alpha, t->tau_f, t->M_phi, t->M_psi, t->gamma, t->h);
+}
 
 int resolve_kind(const tlbm* t) {
     if (t->kind_req == TLBM_KERNEL_SPLIT) return tlbm_host::KIND_SPLIT;
@@ -84,7 +86,7 @@ int mass_blocks() { return kMassBlocks; }
 
 PhysD make_phys(const double kappa[3], double alpha, double tau_f, double M_phi, double M_psi,
                 const double gamma[2], const double h[3]) {
-    PhysD p;
+    PhysD p{};
     const double k1 = kappa[0], k2 = kappa[1], k3 = kappa[2];
     for (int m = 0; m < 3; ++m) p.kappa[m] = kappa[m];
     p.a2 = alpha * alpha;
@@ -159,6 +161,7 @@ void tlbm_destroy(tlbm* t) {
     cudaFree(t->d.step_mass);
     cudaFree(t->d.mass_tmp);
     cudaFree(t->d.flag);
+    cudaFree(t->d.check);
     cudaFree(t->staging);
     if (t->ev[0]) cudaEventDestroy(t->ev[0]);
     if (t->ev[1]) cudaEventDestroy(t->ev[1]);
@@ -280,10 +283,12 @@ tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz
     if (e == cudaSuccess) e = cudaMalloc(&d.step_mass, sizeof(double) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&d.mass_tmp, sizeof(double) * 3);
     if (e == cudaSuccess) e = cudaMalloc(&d.flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&d.check, sizeof(unsigned long long));
     if (e != cudaSuccess) return bail(fail(t, TLBM_ERR_OOM, "cudaMalloc(reductions): %s", cudaGetErrorString(e)));
     const double nan3[3] = {NAN, NAN, NAN};
     e = cudaMemcpy(d.step_mass, nan3, sizeof nan3, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(d.flag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d.check, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamSynchronize(t->st);
     if (e != cudaSuccess) return bail(fail(t, TLBM_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e)));
     *out = t;
@@ -317,10 +322,28 @@ tlbm_kernel tlbm_get_kernel(const tlbm* t) {
 // Tile choice of the fused step: variant (0 = default) and planes per chunk (0 = auto).
 tlbm_status tlbm_set_tile(tlbm* t, int variant, int chunk) {
     if (!t) return TLBM_ERR_ARG;
-    if (variant < 0 || variant > 255 || (variant & 15) > 8 || chunk < 0 || chunk > 4096)
+    if (variant < 0 || variant > 255 || (variant & 15) > 6 || chunk < 0 || chunk > 4096)
         return fail(t, TLBM_ERR_ARG, "bad tile");
     t->d.tile = variant + 256 * chunk;
     // partial sums must fit: blocks grow as chunks shrink
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_set_bounds_check(tlbm* t, int on) {
+    if (!t) return TLBM_ERR_ARG;
+    if (on && t->d.prec != TLBM_FP32)
+        return fail(t, TLBM_ERR_UNSUPPORTED, "bounds-checked kernels exist for TLBM_FP32 storage only");
+    t->d.checked = on ? 1 : 0;
+    return TLBM_OK;
+}
+
+tlbm_status tlbm_bounds_check_word(tlbm* t, uint64_t* word) {
+    if (!t || !word) return TLBM_ERR_ARG;
+    unsigned long long w = 0;
+    CK(cudaStreamSynchronize(t->st));
+    CK(cudaMemcpy(&w, t->d.check, sizeof w, cudaMemcpyDeviceToHost));
+    if (w) CK(cudaMemset(t->d.check, 0, sizeof w));
+    *word = (uint64_t)w;
     return TLBM_OK;
 }
 
@@ -721,7 +744,7 @@ int64_t tlbm_batch_blocks(const tlbm_batch* b) { return b ? (int64_t)b->bs.block
 
 tlbm_status tlbm_batch_set_tile(tlbm_batch* b, int variant, int chunk) {
     if (!b) return TLBM_ERR_ARG;
-    if (variant < 0 || variant > 255 || (variant & 15) > 8 || chunk < 0 || chunk > 4096)
+    if (variant < 0 || variant > 255 || (variant & 15) > 6 || chunk < 0 || chunk > 4096)
         return bfail(b, TLBM_ERR_ARG, "bad tile");
     const int old = b->bs.tile;
     b->bs.tile = variant + 256 * chunk;

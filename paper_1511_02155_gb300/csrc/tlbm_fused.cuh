@@ -45,7 +45,40 @@ struct MGeom {
     int NC;               // chunks along m; chunk c holds planes [c NM / NC, (c+1) NM / NC)
     int tilesA, tilesB;   // tiles per plane
     long long rowstride;  // bytes between consecutive (b, m) rows: ncx * chunk bytes
+    long long bytes;      // bytes of one population buffer (bounds-checked kernels)
+    unsigned long long* check;  // first bounds violation (bounds-checked kernels)
 };
+
+// Bounds checks of the checked kernel variants (CHK).  A violation is recorded
+// as (code << 56 | offset) in *g.check -- the first one wins -- and the access
+// is redirected to a valid address; nothing traps.  Codes: 1 pull source,
+// 2 bounce-back source, 3 store target, 4 moment-ring index, 5 mask index.
+__device__ __forceinline__ void chk_record(const MGeom& g, unsigned code, long long v) {
+    atomicCAS(g.check, 0ull, ((unsigned long long)code << 56) | ((unsigned long long)v & 0x00ffffffffffffffull));
+}
+// a node pointer (chunk + lane * ESZ) of a population buffer starting at base
+template <int Q, typename S, bool CHK, typename P>
+__device__ __forceinline__ P* chk_node(const MGeom& g, P* base, P* p, unsigned code) {
+    if constexpr (CHK) {
+        const long long off = (const unsigned char*)p - (const unsigned char*)base;
+        if (off < 0 || off >= g.bytes || (off % Fmt<Q, S>::CHUNK) >= 32LL * Fmt<Q, S>::ESZ) {
+            chk_record(g, code, off);
+            return base;
+        }
+    }
+    return p;
+}
+// an index into an array of n entries
+template <bool CHK>
+__device__ __forceinline__ long long chk_index(const MGeom& g, long long i, long long n, unsigned code) {
+    if constexpr (CHK) {
+        if (i < 0 || i >= n) {
+            chk_record(g, code, i);
+            return 0;
+        }
+    }
+    return i;
+}
 
 __device__ __forceinline__ int modp(int v, int n) {
     v %= n;
@@ -62,32 +95,35 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// FP32 load of one stored population with an L1 eviction priority:
-// POL 1 evict_last, 2 no_allocate, 3 evict_first (0: a plain load).
-template <int POL>
-__device__ __forceinline__ float ld_l1(const unsigned char* p) {
-    float v;
-    if constexpr (POL == 1) asm("ld.global.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    else if constexpr (POL == 2) asm("ld.global.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    else if constexpr (POL == 3) asm("ld.global.L1::evict_first.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    else v = *reinterpret_cast<const float*>(p);
-    return v;
-}
-
 // ILP: a thread's border node loads interleave with its own node's loads.
 // EARLY: phase C's loads are issued before phase M's (values held across M).
 // PF: each warp prefetches its own 32-node chunk three planes ahead into L2.
 // HINT: 1 streams the stores out (evict-first); 2 also marks phase C's loads,
 //       the last use of those lines, evict-first.
-// STG: the first STG population sets (f, g, k) of a thread's own node, pulled
-//      in phase M, are kept in shared memory (stg: 2 plane slots x STG x Q x NT
-//      values) and the collision reads them from there instead of pulling
-//      them again from L2.
-// L1H (FP32 storage): phase M keeps its own-node lines in L1 (evict_last),
-//      border-node loads do not allocate in L1, and the collision's loads are
-//      their last use (evict_first).
+// STG: STG of the 3Q pulled populations of a thread's own node, loaded in
+//      phase M, are kept in shared memory (2 plane slots x STG x NT values) and
+//      the collision reads them from there instead of pulling them again from
+//      L2; stage_rank orders the candidates (STGO 0: the lane-shifted
+//      directions first, whose warp loads span two chunks; 1: set by set).
+// position of population (s, i) in the staging order: STGO 1 set by set; STGO 0
+// the lane-shifted directions (e_x != 0) of all three sets first
+template <int Q, int STGO>
+__host__ __device__ constexpr int stage_rank(int s, int i) {
+    if (STGO == 1) return s * Q + i;
+    if (Q == 19) {
+        const bool sh = (i == 1 || i == 2) || (i >= 7 && i <= 10) || (i >= 15);
+        const int is = i <= 2 ? i - 1 : (i <= 10 ? i - 5 : i - 9);
+        const int iu = i == 0 ? 0 : (i <= 6 ? i - 2 : i - 6);
+        return sh ? s * 10 + is : 30 + s * 9 + iu;
+    }
+    const bool sh = i == 1 || i == 2 || i >= 5;
+    const int is = i <= 2 ? i - 1 : i - 3;
+    const int iu = i == 0 ? 0 : i - 2;
+    return sh ? s * 6 + is : 18 + s * 3 + iu;
+}
+
 template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false, int HINT = 0, int STG = 0,
-          int L1H = 0>
+          int STGO = 1, bool CHK = false>
 __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__ src, S* __restrict__ dst,
                                            const Phys<typename Store<S>::T>& P, double* __restrict__ partials,
                                            const int bid) {
@@ -137,14 +173,17 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
         } else if (tid < 2 * HW) {
             hx[1] = tid - HW;
             hy[1] = HH - 1;
-        } else {
+        } else if (tid < NBORDER) {
             const int k = tid - 2 * HW;
             hx[1] = k < HH - 2 ? 0 : HW - 1;
             hy[1] = 1 + (k < HH - 2 ? k : k - (HH - 2));
+        } else {  // no border node: node 1 repeats node 0 (never used)
+            hx[1] = hx[0];
+            hy[1] = hy[0];
         }
 #pragma unroll
         for (int n = 0; n < 2; ++n) {
-            h[n] = hy[n] * HW + hx[n];
+            h[n] = (int)chk_index<CHK>(g, hy[n] * HW + hx[n], HN, 4);
             const int aa = modp(A0 + hx[n] - 1, g.NA);
             const int bb = (D == 3) ? modp(B0 + hy[n] - HY, g.NB) : 0;
             const int xs[3] = {wrap1(aa - 1, g.NA), aa, wrap1(aa + 1, g.NA)};
@@ -158,22 +197,12 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
     const int nnodes = tid < NBORDER ? 2 : 1;
 
     const unsigned char* srcb = reinterpret_cast<const unsigned char*>(src);
-    // stored value (x - bias) of (s, i) at node pointer p; pol selects the L1
-    // policy of the L1H variant (1 own node in phase M, 2 border node, 3 collision)
-    auto ldp = [&](const unsigned char* p, int s, int i, int pol) -> T {
-        if constexpr (L1H != 0 && sizeof(S) == 4) {
-            const unsigned char* q = p + Fmt<Q, S>::off(s, i);
-            if (pol == 1) return ld_l1<1>(q);
-            if (pol == 2) return ld_l1<2>(q);
-            return ld_l1<3>(q);
-        } else {
-            return Fmt<Q, S>::ld_delta(p, s, i);
-        }
-    };
+    // stored value (x - bias) of (s, i) at node pointer p
+    auto ldp = [&](const unsigned char* p, int s, int i) -> T { return Fmt<Q, S>::ld_delta(p, s, i); };
     // pull source of direction (ca, cb, cm) for node n at plane rows zr
     auto src_of = [&](int n, const int (&zr)[3], int ca, int cb, int cm) -> const unsigned char* {
         const long long row = (long long)zr[1 - cm] * g.NB + yb[n][1 - cb];
-        return srcb + row * g.rowstride + xc[n][1 - ca];
+        return chk_node<Q, S, CHK>(g, srcb, srcb + row * g.rowstride + xc[n][1 - ca], 1);
     };
 
     // Phase M: moments of plane m for this thread's nodes into ring slot `slot`;
@@ -188,9 +217,9 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const unsigned char* p0 = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
-            const T f = ldp(p0, 0, i, 1);
-            const T gg = ldp(p0, 1, i, 1);
-            const T kk = ldp(p0, 2, i, 1);
+            const T f = ldp(p0, 0, i);
+            const T gg = ldp(p0, 1, i);
+            const T kk = ldp(p0, 2, i);
             rho0 += f;
             if (A::ca(i)) ja += T(A::ca(i)) * f;
             if (A::cb(i)) jb += T(A::cb(i)) * f;
@@ -198,29 +227,31 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
             phi0 += gg;
             psi0 += kk;
             if constexpr (STG > 0) {
-                T* sp = stg + ((size_t)((m & 1) * STG) * Q + i) * NT + tid;
-                sp[0] = f;
-                if (STG > 1) sp[(size_t)Q * NT] = gg;
-                if (STG > 2) sp[(size_t)2 * Q * NT] = kk;
+                T* sp = stg + (size_t)((m & 1) * STG) * NT + tid;
+                const int r0 = stage_rank<Q, STGO>(0, i), r1 = stage_rank<Q, STGO>(1, i),
+                              r2 = stage_rank<Q, STGO>(2, i);
+                if (r0 < STG) sp[(size_t)r0 * NT] = f;
+                if (r1 < STG) sp[(size_t)r1 * NT] = gg;
+                if (r2 < STG) sp[(size_t)r2 * NT] = kk;
             }
             if (ILP && two) {  // border node of this thread, loads interleaved with node 0
                 const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                rho1 += ldp(p1, 0, i, 2);
-                phi1 += ldp(p1, 1, i, 2);
-                psi1 += ldp(p1, 2, i, 2);
+                rho1 += ldp(p1, 0, i);
+                phi1 += ldp(p1, 1, i);
+                psi1 += ldp(p1, 2, i);
             }
         }
         if (!ILP && two) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                rho1 += ldp(p1, 0, i, 2);
-                phi1 += ldp(p1, 1, i, 2);
-                psi1 += ldp(p1, 2, i, 2);
+                rho1 += ldp(p1, 0, i);
+                phi1 += ldp(p1, 1, i);
+                psi1 += ldp(p1, 2, i);
             }
         }
         rd = rho0;
-        if (Fmt<Q, S>::PACKED) {  // sums of f deviations: rho - 1
+        if (Fmt<Q, S>::OFFSET) {  // sums of f deviations: rho - 1
             rho0 += T(1);
             rho1 += T(1);
         }
@@ -248,24 +279,28 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
         // phase-M loads of plane m+1 so that both sets of requests are in flight
         // together (these were read one iteration ago and hit in L2).
         const int zr[3] = {wrap1(m - 1, g.NM), m, wrap1(m + 1, g.NM)};
+        // stored values (deviations x - bias: the 16-bit formats keep f as f_i - w_i;
+        // the collision below works on deviations, with the bias folded into its
+        // constants)
         T fv[Q], gv[Q], kv[Q];
         auto load_node = [&]() {
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const unsigned char* pi = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
-                if constexpr (STG > 0 || L1H != 0) {
-                    const T* sp = stg + ((size_t)((m & 1) * STG) * Q + i) * NT + tid;
-                    fv[i] = (STG > 0 ? sp[0] : ldp(pi, 0, i, 3)) + T(Fmt<Q, S>::bias(0, i));
-                    gv[i] = (STG > 1 ? sp[(size_t)Q * NT] : ldp(pi, 1, i, 3)) + T(Fmt<Q, S>::bias(1, i));
-                    kv[i] = (STG > 2 ? sp[(size_t)2 * Q * NT] : ldp(pi, 2, i, 3)) + T(Fmt<Q, S>::bias(2, i));
-                } else if (HINT >= 2) {
-                    fv[i] = Fmt<Q, S>::ld_last(pi, 0, i);
-                    gv[i] = Fmt<Q, S>::ld_last(pi, 1, i);
-                    kv[i] = Fmt<Q, S>::ld_last(pi, 2, i);
+                auto lc = [&](int s_) -> T {
+                    return HINT >= 2 ? Fmt<Q, S>::ld_last_delta(pi, s_, i) : Fmt<Q, S>::ld_delta(pi, s_, i);
+                };
+                if constexpr (STG > 0) {
+                    const T* sp = stg + (size_t)((m & 1) * STG) * NT + tid;
+                    const int r0 = stage_rank<Q, STGO>(0, i), r1 = stage_rank<Q, STGO>(1, i),
+                              r2 = stage_rank<Q, STGO>(2, i);
+                    fv[i] = r0 < STG ? sp[(size_t)r0 * NT] : lc(0);
+                    gv[i] = r1 < STG ? sp[(size_t)r1 * NT] : lc(1);
+                    kv[i] = r2 < STG ? sp[(size_t)r2 * NT] : lc(2);
                 } else {
-                    fv[i] = Fmt<Q, S>::ld(pi, 0, i);
-                    gv[i] = Fmt<Q, S>::ld(pi, 1, i);
-                    kv[i] = Fmt<Q, S>::ld(pi, 2, i);
+                    fv[i] = lc(0);
+                    gv[i] = lc(1);
+                    kv[i] = lc(2);
                 }
             }
         };
@@ -292,8 +327,8 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
             for (int i = 1; i < Q; ++i) {
                 if (opp<Q>(i) < i) continue;
                 const int sp = (m + A::cm(i)) & 3, sn = (m - A::cm(i)) & 3;
-                const int cp = c0 + A::cb(i) * HW + A::ca(i);
-                const int cn = c0 - A::cb(i) * HW - A::ca(i);
+                const int cp = (int)chk_index<CHK>(g, c0 + A::cb(i) * HW + A::ca(i), HN, 4);
+                const int cn = (int)chk_index<CHK>(g, c0 - A::cb(i) * HW - A::ca(i), HN, 4);
                 const T w = T(Lat<Q>::w(i));
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -320,25 +355,31 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
                 }
             }
             NodeEq<Q, T> E;
-            if (D == 3) E.setup(P, X0[0], jc[0], jc[1], jc[2], X0[1], X0[2], grad, lap);
-            else E.setup(P, X0[0], jc[0], jc[2], T(0), X0[1], X0[2], grad, lap);
+            if (D == 3) E.setup(P, X0[0], jc[0], jc[1], jc[2], X0[1], X0[2], grad, lap, rdc);
+            else E.setup(P, X0[0], jc[0], jc[2], T(0), X0[1], X0[2], grad, lap, rdc);
             mr += rho_total<Q, S>(rdc);
             mp += (double)X0[1];
             ms += (double)X0[2];
 
             // ---- collide + store, direction pairs
-            unsigned char* out = reinterpret_cast<unsigned char*>(dst) +
-                                 ((long long)m * g.NB + yb[0][1]) * g.rowstride + xc[0][1];
+            unsigned char* out = chk_node<Q, S, CHK>(
+                g, reinterpret_cast<unsigned char*>(dst),
+                reinterpret_cast<unsigned char*>(dst) + ((long long)m * g.NB + yb[0][1]) * g.rowstride + xc[0][1], 3);
 
-            auto st_ = [&](unsigned char* o, int ss, int ii, T v) {
-                if (HINT >= 1) Fmt<Q, S>::st_stream(o, ss, ii, v);
-                else Fmt<Q, S>::st(o, ss, ii, v);
+            auto st_ = [&](unsigned char* o, int ss, int ii, T d) {
+                if (HINT >= 1) Fmt<Q, S>::st_stream_delta(o, ss, ii, d);
+                else Fmt<Q, S>::st_delta(o, ss, ii, d);
             };
             // BGK with omega folded into the equilibria: x* = (1 - omega) x + omega x_eq,
             // and omega x_eq = EV +- OD for a pair of opposite links, where
-            // EV = w (B + R (e.u)^2) [+ gradient terms for f] and OD = w O (e.u)
+            // EV = w (B + R (e.u)^2) [+ gradient terms for f] and OD = w O (e.u).
+            // On deviations d = x - w b (b = 1 for f in the offset formats, else 0):
+            // d* = (1 - omega) d + EV - omega w b +- OD, i.e. B is lowered by omega b:
+            // B = omega (bf - 1), with bf - 1 formed from rho - 1 (no cancellation).
+            constexpr bool OF = Fmt<Q, S>::OFFSET;
             const T cf = T(1) - P.omega[0], cg = T(1) - P.omega[1], ck = T(1) - P.omega[2];
-            const T Bf = P.omega[0] * E.bf, Rf = T(4.5) * P.omega[0] * E.rho, Of = T(3) * P.omega[0] * E.rho;
+            const T Bf = P.omega[0] * (OF ? E.bf1 : E.bf), Rf = T(4.5) * P.omega[0] * E.rho,
+                    Of = T(3) * P.omega[0] * E.rho;
             const T Bg = P.omega[1] * E.bg, Rg = T(4.5) * P.omega[1] * E.phi, Og = T(3) * P.omega[1] * E.phi;
             const T Bk = P.omega[2] * E.bk, Rk = T(4.5) * P.omega[2] * E.psi, Ok = T(3) * P.omega[2] * E.psi;
 #pragma unroll
@@ -367,18 +408,19 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
                 st_(out, 1, o, v[3]);
                 st_(out, 2, i, v[4]);
                 st_(out, 2, o, v[5]);
-                if (Fmt<Q, S>::PACKED) {
-                    qf += Fmt<Q, S>::qdelta(0, i, v[0]) + Fmt<Q, S>::qdelta(0, o, v[1]);
-                    qg += Fmt<Q, S>::qdelta(1, i, v[2]) + Fmt<Q, S>::qdelta(1, o, v[3]);
-                    qk += Fmt<Q, S>::qdelta(2, i, v[4]) + Fmt<Q, S>::qdelta(2, o, v[5]);
+                if (OF) {
+                    qf += Fmt<Q, S>::qdelta_d(i, v[0]) + Fmt<Q, S>::qdelta_d(o, v[1]);
+                    qg += Fmt<Q, S>::qdelta_d(i, v[2]) + Fmt<Q, S>::qdelta_d(o, v[3]);
+                    qk += Fmt<Q, S>::qdelta_d(i, v[4]) + Fmt<Q, S>::qdelta_d(o, v[5]);
                 }
             }
-            if (Fmt<Q, S>::PACKED) {
-                // rest = moment - stored moving populations (deviations for f):
-                // conserves rho, phi, psi through the 16-bit rounding
-                Fmt<Q, S>::st_delta(out, 0, 0, rdc - qf);
-                Fmt<Q, S>::st_delta(out, 1, 0, E.phi - qg);
-                Fmt<Q, S>::st_delta(out, 2, 0, E.psi - qk);
+            if (OF) {
+                // rest = moment - moving populations as stored (deviations for f):
+                // every node keeps its rho, phi, psi through the rounding of the
+                // stored values (a rounding of the rest population alone)
+                st_(out, 0, 0, rdc - qf);
+                st_(out, 1, 0, E.phi - qg);
+                st_(out, 2, 0, E.psi - qk);
             } else {
                 // omega x_eq_0 = omega X - sum of omega x_eq over the moving links
                 st_(out, 0, 0, cf * fv[0] + (P.omega[0] * E.rho - sf));
@@ -391,7 +433,6 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
         jc[2] = jn[2];
         rdc = rdn;
     }
-
     block_sum3(mr, mp, ms);
     if (tid == 0) {
         partials[3 * bid + 0] = mr;
@@ -400,20 +441,21 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
     }
 }
 
-template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false, int HINT = 0>
+template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false, int HINT = 0, bool CHK = false>
 __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))  // 16 warps per SM
 k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename Store<S>::T> P,
         double* __restrict__ partials) {
-    fused_body<Q, S, TX, TY, ILP, EARLY, PF, HINT>(g, src, dst, P, partials, blockIdx.x);
+    fused_body<Q, S, TX, TY, ILP, EARLY, PF, HINT, 0, 1, CHK>(g, src, dst, P, partials, blockIdx.x);
 }
 
 // Variants of the periodic step with shared-memory staging of the pulled
-// populations (STG sets) or L1 eviction priorities (L1H), at BPS blocks per SM.
-template <int Q, typename S, int TX, int TY, int STG, int L1H, int BPS>
+// populations (STG values in the order STGO), at BPS blocks per SM.
+template <int Q, typename S, int TX, int TY, int STG, int STGO, int BPS, bool ILP, bool PF, int HINT,
+          bool CHK = false>
 __global__ void __launch_bounds__(TX * TY, BPS)
 k_fused_x(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename Store<S>::T> P,
           double* __restrict__ partials) {
-    fused_body<Q, S, TX, TY, false, false, false, 1, STG, L1H>(g, src, dst, P, partials, blockIdx.x);
+    fused_body<Q, S, TX, TY, ILP, false, PF, HINT, STG, STGO, CHK>(g, src, dst, P, partials, blockIdx.x);
 }
 
 // ------------------------------------------------------ solid-aware variant
@@ -448,7 +490,7 @@ __global__ void k_nbmask(Geom g, const uint8_t* __restrict__ solid, uint32_t* __
 //   C(m):   derivatives, equilibria, BGK and store for the fluid tile nodes.
 // The moment and mask rings have five plane slots and the momentum ring four, so
 // a fast warp writing plane m+2 never touches data a slow warp still reads.
-template <int Q, typename S, int TX, int TY>
+template <int Q, typename S, int TX, int TY, bool CHK = false>
 __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__ src, S* __restrict__ dst,
                                            const uint32_t* __restrict__ nbm,
                                            const Phys<typename Store<S>::T>& P, double* __restrict__ partials,
@@ -527,15 +569,16 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
         for (int k = 0; k < KS; ++k) {
             const int h = tid + k * NT;
             if (h >= HN) break;
-            const uint32_t mk = nbm[(long long)mm * plane + rin[k]];
+            const uint32_t mk = nbm[chk_index<CHK>(g, (long long)mm * plane + rin[k], plane * g.NM, 5)];
             T rd = T(0), ja = T(0), jb = T(0), jm = T(0), phi = T(0), psi = T(0);
             if (!(mk & 1u)) {
-                const unsigned char* own = row_ptr(k, zr, 0, 0) + xc[k][1];
+                const unsigned char* own = chk_node<Q, S, CHK>(g, srcb, row_ptr(k, zr, 0, 0) + xc[k][1], 2);
 #pragma unroll
                 for (int i = 0; i < Q; ++i) {
                     // pull source, or this node's opposite run when the source is solid:
                     // one pointer select, then loads at the run offsets of direction i
-                    const unsigned char* p = row_ptr(k, zr, A::cb(i), A::cm(i)) + xc[k][1 - A::ca(i)];
+                    const unsigned char* p =
+                        chk_node<Q, S, CHK>(g, srcb, row_ptr(k, zr, A::cb(i), A::cm(i)) + xc[k][1 - A::ca(i)], 1);
                     if (i > 0 && ((mk >> i) & 1u)) p = own + Fmt<Q, S>::run_gap(i, opp<Q>(i));
                     const T f = Fmt<Q, S>::ld_delta(p, 0, i);
                     rd += f;
@@ -546,7 +589,7 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
                     psi += Fmt<Q, S>::ld_delta(p, 2, i);
                 }
             }
-            const T rho = (mk & 1u) ? T(0) : (Fmt<Q, S>::PACKED ? T(1) + rd : rd);
+            const T rho = (mk & 1u) ? T(0) : (Fmt<Q, S>::OFFSET ? T(1) + rd : rd);
             sm[slot][0][h] = rho;
             sm[slot][1][h] = phi;
             sm[slot][2][h] = psi;
@@ -579,7 +622,7 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
             for (int i = 1; i <= Lat<Q>::NAXIS; ++i) {  // neighbour s + e_i is fluid?
                 if ((mk >> opp<Q>(i)) & 1u) continue;
                 const int sn = modp(q + A::cm(i), R);
-                const int hn = h + A::cb(i) * HW + A::ca(i);
+                const int hn = (int)chk_index<CHK>(g, h + A::cb(i) * HW + A::ca(i), HN, 4);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) acc[c] += sm[sn][c][hn] - P.Gw[c];
                 ++n;
@@ -590,7 +633,7 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
                 for (int i = Lat<Q>::NAXIS + 1; i < Q; ++i) {
                     if ((mk >> opp<Q>(i)) & 1u) continue;
                     const int sn = modp(q + A::cm(i), R);
-                    const int hn = h + A::cb(i) * HW + A::ca(i);
+                    const int hn = (int)chk_index<CHK>(g, h + A::cb(i) * HW + A::ca(i), HN, 4);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) acc[c] += sm[sn][c][hn] - r2 * P.Gw[c];
                     ++n;
@@ -633,8 +676,8 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
         for (int i = 1; i < Q; ++i) {
             if (opp<Q>(i) < i) continue;
             const int sp = modp(m + A::cm(i), R), sn = modp(m - A::cm(i), R);
-            const int cp = c0 + A::cb(i) * HW + A::ca(i);
-            const int cn = c0 - A::cb(i) * HW - A::ca(i);
+            const int cp = (int)chk_index<CHK>(g, c0 + A::cb(i) * HW + A::ca(i), HN, 4);
+            const int cn = (int)chk_index<CHK>(g, c0 - A::cb(i) * HW - A::ca(i), HN, 4);
             const T w = T(Lat<Q>::w(i));
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -671,11 +714,11 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
 
         // ---- pulled populations (bounce-back at solid sources)
         const int zr[3] = {wrap1(m - 1, g.NM), m, wrap1(m + 1, g.NM)};
-        const unsigned char* own = own_row(zr, 0, 0) + xo[1];
+        const unsigned char* own = chk_node<Q, S, CHK>(g, srcb, own_row(zr, 0, 0) + xo[1], 2);
         T fv[Q], gv[Q], kv[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const unsigned char* p = own_row(zr, A::cb(i), A::cm(i)) + xo[1 - A::ca(i)];
+            const unsigned char* p = chk_node<Q, S, CHK>(g, srcb, own_row(zr, A::cb(i), A::cm(i)) + xo[1 - A::ca(i)], 1);
             if (i > 0 && ((mk >> i) & 1u)) p = own + Fmt<Q, S>::run_gap(i, opp<Q>(i));
             fv[i] = Fmt<Q, S>::ld(p, 0, i);
             gv[i] = Fmt<Q, S>::ld(p, 1, i);
@@ -683,7 +726,9 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
         }
 
         // ---- collide + store (same arithmetic as k_fused)
-        unsigned char* out = reinterpret_cast<unsigned char*>(dst) + ((long long)m * g.NB + yo[1]) * g.rowstride + xo[1];
+        unsigned char* out = chk_node<Q, S, CHK>(
+            g, reinterpret_cast<unsigned char*>(dst),
+            reinterpret_cast<unsigned char*>(dst) + ((long long)m * g.NB + yo[1]) * g.rowstride + xo[1], 3);
         const T cf = T(1) - P.omega[0], cg = T(1) - P.omega[1], ck = T(1) - P.omega[2];
         const T Bf = P.omega[0] * E.bf, Rf = T(4.5) * P.omega[0] * E.rho, Of = T(3) * P.omega[0] * E.rho;
         const T Bg = P.omega[1] * E.bg, Rg = T(4.5) * P.omega[1] * E.phi, Og = T(3) * P.omega[1] * E.phi;
@@ -713,13 +758,13 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
             Fmt<Q, S>::st(out, 1, o, v[3]);
             Fmt<Q, S>::st(out, 2, i, v[4]);
             Fmt<Q, S>::st(out, 2, o, v[5]);
-            if (Fmt<Q, S>::PACKED) {
+            if (Fmt<Q, S>::OFFSET) {
                 qf += Fmt<Q, S>::qdelta(0, i, v[0]) + Fmt<Q, S>::qdelta(0, o, v[1]);
                 qg += Fmt<Q, S>::qdelta(1, i, v[2]) + Fmt<Q, S>::qdelta(1, o, v[3]);
                 qk += Fmt<Q, S>::qdelta(2, i, v[4]) + Fmt<Q, S>::qdelta(2, o, v[5]);
             }
         }
-        if (Fmt<Q, S>::PACKED) {
+        if (Fmt<Q, S>::OFFSET) {
             Fmt<Q, S>::st_delta(out, 0, 0, rdc - qf);
             Fmt<Q, S>::st_delta(out, 1, 0, E.phi - qg);
             Fmt<Q, S>::st_delta(out, 2, 0, E.psi - qk);
@@ -738,11 +783,11 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
     }
 }
 
-template <int Q, typename S, int TX, int TY>
+template <int Q, typename S, int TX, int TY, bool CHK = false>
 __global__ void __launch_bounds__(TX * TY, 512 / (TX * TY))
 k_fused_solid(MGeom g, const S* __restrict__ src, S* __restrict__ dst, const uint32_t* __restrict__ nbm,
               Phys<typename Store<S>::T> P, double* __restrict__ partials) {
-    solid_body<Q, S, TX, TY>(g, src, dst, nbm, P, partials, blockIdx.x);
+    solid_body<Q, S, TX, TY, CHK>(g, src, dst, nbm, P, partials, blockIdx.x);
 }
 
 // ------------------------------------------------------------- batches
@@ -827,28 +872,30 @@ inline int grid_of(long long n, int sms) {
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-// tile variants: 0 = default (D3Q19 32x4, D2Q9 128); D3Q19: 1 = 32x8, 2 = 64x4, 3 = 32x4;
-// D2Q9: 1 = 128, 2 = 256, 3 = 64.  tile = variant + 16 * chunk (chunk 0 = auto).
 template <int Q>
 struct FusedCfg {
     int TX, TY, MC;
     int mode;
-    int shape;  // resolved shape (D3Q19 4..8: 32x4 variants of k_fused_x)
+    int shape;  // resolved D3Q19 shape (4..6: 32x4 kernels with staging)
 };
 
-// d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 32x4,
-// D2Q9 128); D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4; D2Q9 1 = 128, 2 = 256,
-// 3 = 64.  mode bit 0: interleaved border loads; bit 1: early phase-C loads;
-// bit 2: per-warp L2 prefetch three planes ahead; 8 / 9: evict-first stores /
-// stores and collision loads (12, 13 with the prefetch).  mode 0 is the
-// default for the shape and format (D3Q19 32x4: 8 for FP32, 12 for 16-bit
-// storage; other D3Q19: 1; D2Q9: 13); 6 selects the plain loop.  chunk = planes
-// per block (0 = chosen from the lattice size).
+// d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 shape 5,
+// D2Q9 128); D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4, 4..6 = 32x4 with the pulled
+// populations of a thread's node staged in shared memory for the collision
+// (4: the 19 f values; 5: lane-shifted values first, 28 for FP32, 19 with the
+// per-warp prefetch for 16-bit storage; 6: 19 lane-shifted values); D2Q9 1 =
+// 128, 2 = 256, 3 = 64.  mode (shapes 1..3 and D2Q9) bit 0: interleaved border
+// loads; bit 1: early phase-C loads; bit 2: per-warp L2 prefetch three planes
+// ahead; 8 / 9: evict-first stores / stores and collision loads (12, 13 with
+// the prefetch).  mode 0 is the default for the shape and format (D3Q19 32x4:
+// 8 for FP32, 12 for 16-bit storage; other D3Q19: 1; D2Q9: 13); 6 selects the
+// plain loop.  chunk = planes per block (0 = chosen from the lattice size).
 template <int Q>
 inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
     const bool dbl = d.prec == 0;  // double storage: one default shape only
-    const int variant = dbl ? 0 : (d.tile & 15);
-    int mc = d.tile >> 8;
+    const int tile = d.checked ? 0 : d.tile;  // the checked kernels use the default tile
+    const int variant = dbl ? 0 : (tile & 15);
+    int mc = tile >> 8;
     FusedCfg<Q> c{};
     if (d.solid) {
         // solid-aware kernel: a fixed tile per lattice (D3Q19 in double: 16x4 keeps
@@ -859,7 +906,7 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
         c.TX = 16;  // double storage: a smaller tile keeps the static shared ring small
         c.TY = 8;
     } else if (Q == 19) {
-        const int v = variant == 0 ? 3 : variant;  // 32x4 measured fastest on 256^3
+        const int v = variant == 0 ? 5 : variant;  // 32x4 with staging measured fastest on 256^3
         c.TX = v == 2 ? 64 : 32;
         c.TY = v == 1 ? 8 : 4;
         c.shape = v;
@@ -868,7 +915,7 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
         c.TX = v == 2 ? 256 : (v == 3 ? 64 : 128);
         c.TY = 1;
     }
-    c.mode = dbl ? 0 : ((d.tile >> 4) & 15);
+    c.mode = dbl ? 0 : ((tile >> 4) & 15);
     // defaults measured on GB300: D3Q19 32x4 with evict-first stores, plus a
     // per-warp L2 prefetch for the 16-bit formats (a plane of FP32 populations
     // is too large for the prefetch to stay in L2); 64x4 and 32x8 interleaved
@@ -906,6 +953,8 @@ inline MGeom mgeom(const tlbm_host::DevState& d, const FusedCfg<Q>& c) {
     g.NM = (Q == 19) ? d.nz : d.ny;
     g.rowstride = (long long)d.ncx * Fmt<Q, S>::CHUNK;
     g.NC = (g.NM + c.MC - 1) / c.MC;  // chunks of MC planes or one fewer (balanced)
+    g.bytes = d.pop_bytes;
+    g.check = d.check;
     g.tilesA = (g.NA + c.TX - 1) / c.TX;
     g.tilesB = (g.NB + c.TY - 1) / c.TY;
     return g;
@@ -924,6 +973,25 @@ inline int fused_partials(const tlbm_host::DevState& d, int kind) {
     return kind == tlbm_host::KIND_FUSED ? (int)fused_blocks<Q, S>(d) : kMassBlocks;
 }
 
+// Launch of a kernel with STG staged values per thread of 128 (dynamic shared
+// memory), with the smallest shared-memory carveout that still holds four
+// blocks per SM, so that the rest of the SM's 256 KB stays L1 (which holds the
+// kernel's loads in flight).
+template <typename K, typename... Args>
+inline cudaError_t launch_staged(K kern, int stg, long long nb, cudaStream_t st, Args... args) {
+    const int dyn = stg * 2 * 128 * (int)sizeof(float);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+    const long long need = 4LL * ((long long)fa.sharedSizeBytes + dyn + 1024);
+    const int pct = (int)((need * 100 + 233471) / 233472);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
+    if (e != cudaSuccess) return e;
+    kern<<<(int)nb, 128, dyn, st>>>(args...);
+    return cudaSuccess;
+}
+
 template <int Q, typename S>
 inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<S>::T>& P, cudaStream_t st) {
     const FusedCfg<Q> c = fused_cfg<Q>(d);
@@ -932,12 +1000,33 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
     if (nb > 0x7fffffffLL || nb > d.partials_cap) return cudaErrorInvalidConfiguration;
     const S* src = static_cast<const S*>(d.pop[d.cur]);
     S* dst = static_cast<S*>(d.pop[1 - d.cur]);
-    if (d.solid) {
-        if (!d.nbm_ready) {
-            const Geom gg{d.nx, d.ny, d.nz, d.N, d.Np, d.ncx};
-            k_nbmask<Q><<<grid_of(d.N, d.sms), 256, 0, st>>>(gg, d.solid, d.nbm);
-            d.nbm_ready = 1;
+    if (d.solid && !d.nbm_ready) {
+        const Geom gg{d.nx, d.ny, d.nz, d.N, d.Np, d.ncx};
+        k_nbmask<Q><<<grid_of(d.N, d.sms), 256, 0, st>>>(gg, d.solid, d.nbm);
+        d.nbm_ready = 1;
+    }
+    if (d.checked) {
+        // bounds-checked kernels of the default FP32 tiles (recording, never trapping)
+        if constexpr (sizeof(S) == 4) {
+            if (!d.check) return cudaErrorInvalidValue;
+            if (d.solid) {
+                if constexpr (Q == 19) k_fused_solid<Q, S, 32, 4, true><<<(int)nb, 128, 0, st>>>(g, src, dst, d.nbm, P, d.partials);
+                else k_fused_solid<Q, S, 128, 1, true><<<(int)nb, 128, 0, st>>>(g, src, dst, d.nbm, P, d.partials);
+            } else {
+                if constexpr (Q == 19) {
+                    const cudaError_t e = launch_staged(k_fused_x<Q, S, 32, 4, 28, 0, 4, false, false, 1, true>, 28, nb,
+                                                        st, g, src, dst, P, d.partials);
+                    if (e != cudaSuccess) return e;
+                } else {
+                    k_fused<Q, S, 128, 1, false, false, true, 2, true><<<(int)nb, 128, 0, st>>>(g, src, dst, P, d.partials);
+                }
+            }
+            return cudaGetLastError();
+        } else {
+            return cudaErrorNotSupported;
         }
+    }
+    if (d.solid) {
         auto gos = [&](auto kern, int threads) {
             kern<<<(int)nb, threads, 0, st>>>(g, src, dst, d.nbm, P, d.partials);
         };
@@ -957,27 +1046,27 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
         if constexpr (Q == 19) go(k_fused<Q, S, 16, 8, false, false>, 128);
         else go(k_fused<Q, S, 128, 1, false, false>, 128);
     } else if constexpr (Q == 19) {
-        if constexpr (sizeof(S) == 4) {
+        if constexpr (sizeof(S) <= 4) {
             if (c.shape >= 4) {
-                // 32x4 variants: 4 all sets staged in shared memory, 3 blocks/SM; 5 f and g
-                // staged, 4 blocks/SM; 6 / 7 L1 eviction priorities at 4 / 3 blocks/SM;
-                // 8 the default loop at 3 blocks/SM
-                auto gox = [&](auto kern, int stg, int bps) {
-                    const int dyn = stg * 2 * Q * 128 * (int)sizeof(float);
-                    const int ring = 4 * 3 * 34 * 6 * (int)sizeof(float);
-                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-                    const int pct = (bps * (dyn + ring + 1024) * 100 + 233471) / 233472;
-                    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
-                    kern<<<(int)nb, 128, dyn, st>>>(g, src, dst, P, d.partials);
-                };
-                switch (c.shape) {
-                    case 4: gox(k_fused_x<Q, S, 32, 4, 3, 0, 3>, 3, 3); break;
-                    case 5: gox(k_fused_x<Q, S, 32, 4, 2, 0, 4>, 2, 4); break;
-                    case 6: gox(k_fused_x<Q, S, 32, 4, 1, 0, 4>, 1, 4); break;
-                    case 7: gox(k_fused_x<Q, S, 32, 4, 0, 1, 3>, 0, 3); break;
-                    default: gox(k_fused_x<Q, S, 32, 4, 0, 0, 3>, 0, 3);
+                // 32x4 kernels with shared-memory staging of the pulled populations:
+                // 4 the 19 f values; 5 (default) the lane-shifted values first, 28
+                // of them for FP32, 19 with the per-warp L2 prefetch for the 16-bit
+                // formats; 6 19 lane-shifted values (no prefetch)
+                cudaError_t e;
+                if constexpr (sizeof(S) == 2) {
+                    switch (c.shape) {
+                        case 4: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 1, 4, false, true, 1>, 19, nb, st, g, src, dst, P, d.partials); break;
+                        case 6: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 0, 4, false, false, 1>, 19, nb, st, g, src, dst, P, d.partials); break;
+                        default: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 0, 4, false, true, 1>, 19, nb, st, g, src, dst, P, d.partials);
+                    }
+                } else {
+                    switch (c.shape) {
+                        case 4: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 1, 4, false, false, 1>, 19, nb, st, g, src, dst, P, d.partials); break;
+                        case 6: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 0, 4, false, false, 1>, 19, nb, st, g, src, dst, P, d.partials); break;
+                        default: e = launch_staged(k_fused_x<Q, S, 32, 4, 28, 0, 4, false, false, 1>, 28, nb, st, g, src, dst, P, d.partials);
+                    }
                 }
-                return cudaGetLastError();
+                return e != cudaSuccess ? e : cudaGetLastError();
             }
         }
         if (c.TX == 64) {

@@ -51,6 +51,8 @@ struct DevState {
     PhysD phys;
     int tile;            // fused-kernel tile choice (0 = default)
     int sms;             // multiprocessors of the device (sizes the fused grid's chunks)
+    unsigned long long* check;  // device word: first bounds violation of a checked step
+    int checked;         // 1: the fused step runs its bounds-checked kernels
     long long partials_cap;  // blocks whose partial sums fit in the first part of partials
 };
 

@@ -100,7 +100,7 @@ __device__ __forceinline__ typename Store<S>::T pull_delta(const Geom& g, const 
 // f - w, whose sum is rho - 1)
 template <int Q, typename S>
 __device__ __forceinline__ double rho_total(typename Store<S>::T rd) {
-    return Fmt<Q, S>::PACKED ? 1.0 + (double)rd : (double)rd;
+    return Fmt<Q, S>::OFFSET ? 1.0 + (double)rd : (double)rd;
 }
 
 // ------------------------------------------------- moments (+ mass partials)
@@ -271,7 +271,7 @@ k_collide_split(Geom g, const S* __restrict__ src, S* __restrict__ dst,
             phi += gg[i];
             psi += k[i];
         }
-        const T rho = Fmt<Q, S>::PACKED ? T(1) + rd : rd;
+        const T rho = Fmt<Q, S>::OFFSET ? T(1) + rd : rd;
         T grad[3][3], lap[3];
         derivs<Q, T>(g, mom, x, y, z, r, grad, lap);
         NodeEq<Q, T> E;
@@ -289,15 +289,15 @@ k_collide_split(Geom g, const S* __restrict__ src, S* __restrict__ dst,
             Fmt<Q, S>::st(cb, 0, i, vf);
             Fmt<Q, S>::st(cb, 1, i, vg);
             Fmt<Q, S>::st(cb, 2, i, vk);
-            if (Fmt<Q, S>::PACKED) {
+            if (Fmt<Q, S>::OFFSET) {
                 qf += Fmt<Q, S>::qdelta(0, i, vf);
                 qg += Fmt<Q, S>::qdelta(1, i, vg);
                 qk += Fmt<Q, S>::qdelta(2, i, vk);
             }
         }
-        if (Fmt<Q, S>::PACKED) {
-            // rest = moment - stored moving populations (deviations for f):
-            // conserves rho, phi, psi through the 16-bit rounding
+        if (Fmt<Q, S>::OFFSET) {
+            // rest = moment - moving populations as stored (deviations for f):
+            // every node keeps its rho, phi, psi through the storage rounding
             Fmt<Q, S>::st_delta(cb, 0, 0, rd - qf);
             Fmt<Q, S>::st_delta(cb, 1, 0, phi - qg);
             Fmt<Q, S>::st_delta(cb, 2, 0, psi - qk);

@@ -149,7 +149,10 @@ struct Store<__nv_bfloat16> {
 // Fmt<Q,S>::CHUNK bytes at ((row * ncx + c) * CHUNK), ncx = ceil(nx / 32).
 // Inside a chunk, each run holds one value per lane (node), sizeof(S) bytes
 // apart, so a node is one byte offset: chunk + lane * sizeof(S).
-//   FP64 / FP32: 3Q runs of S, run s*Q + i for set s, direction i.
+//   FP64 / FP32: 3Q runs of S, run s*Q + i for set s, direction i.  FP32 keeps
+//     f as its deviation f_i - w_i from the rest state at rho = 1 (g and k as
+//     they are): deviations are small, so FP32 rounding of the stored values,
+//     and with it the drift of the total momentum, is ~100x smaller.
 //   16-bit formats (packed): f is kept as its deviation f_i - w_i from the
 //     rest state at rho = 1, g and k as they are.  The 3(Q-1) moving directions
 //     i >= 1 are 16-bit runs; the rest populations f_0 - w_0, g_0, k_0 are FP32,
@@ -174,6 +177,9 @@ template <int Q, typename S>
 struct Fmt {
     using T = typename Store<S>::T;
     static constexpr bool PACKED = sizeof(S) == 2;
+    // f kept as its deviation f_i - w_i from the rest state at rho = 1 (FP32 and
+    // the 16-bit formats; FP64 stores f as it is)
+    static constexpr bool OFFSET = sizeof(S) <= 4;
     static constexpr int ESZ = (int)sizeof(S);  // bytes between lanes of a run
     static constexpr long long CHUNK = PACKED ? (3LL * Q + 3) * 32 * 2 : 3LL * Q * 32 * ESZ;
     // byte offset of lane 0 of the run of (s, i) (packed rest: its low halves)
@@ -186,7 +192,7 @@ struct Fmt {
     __host__ __device__ static constexpr int run_gap(int i, int j) { return off(0, j) - off(0, i); }
     // rest-state value subtracted before storage (packed formats, set f)
     __host__ __device__ static constexpr double bias(int s, int i) {
-        return (PACKED && s == 0) ? Lat<Q>::w(i) : 0.0;
+        return (OFFSET && s == 0) ? Lat<Q>::w(i) : 0.0;
     }
     // stored value of (s, i) at node pointer n (chunk + lane * ESZ): x - bias
     static __device__ __forceinline__ T ld_delta(const unsigned char* n, int s, int i) {
@@ -201,27 +207,56 @@ struct Fmt {
             return *reinterpret_cast<const S*>(n + off(s, i));
         }
     }
-    // population (s, i) at node pointer n
+    // population (s, i) at node pointer n (no add where the bias is zero: x + 0
+    // is not x for x = -0, so the compiler would keep it)
     static __device__ __forceinline__ T ld(const unsigned char* n, int s, int i) {
-        return ld_delta(n, s, i) + T(bias(s, i));
+        const double b = bias(s, i);
+        return b == 0.0 ? ld_delta(n, s, i) : ld_delta(n, s, i) + T(b);
     }
     // the same, marking the line evict-first (its last use in this kernel)
     static __device__ __forceinline__ T ld_last(const unsigned char* n, int s, int i) {
+        const double b = bias(s, i);
+        return b == 0.0 ? ld_last_delta(n, s, i) : ld_last_delta(n, s, i) + T(b);
+    }
+    // stored value of (s, i), marking the line evict-first (its last use)
+    static __device__ __forceinline__ T ld_last_delta(const unsigned char* n, int s, int i) {
         if constexpr (PACKED) {
             if (i == 0) {
                 const unsigned lo = __ldcs(reinterpret_cast<const unsigned short*>(n + off(s, 0)));
                 const unsigned hi = __ldcs(reinterpret_cast<const unsigned short*>(n + off(s, 0) + 64));
-                return __uint_as_float(lo | (hi << 16)) + T(bias(s, 0));
+                return __uint_as_float(lo | (hi << 16));
             }
-            return Store<S>::get(__ldcs(reinterpret_cast<const S*>(n + off(s, i)))) + T(bias(s, i));
+            return Store<S>::get(__ldcs(reinterpret_cast<const S*>(n + off(s, i))));
         } else {
             return __ldcs(reinterpret_cast<const S*>(n + off(s, i)));
         }
     }
+    // store the deviation d of (s, i) with an evict-first hint
+    static __device__ __forceinline__ void st_stream_delta(unsigned char* n, int s, int i, T d) {
+        if constexpr (PACKED) {
+            if (i == 0) {
+                const unsigned u = __float_as_uint(d);
+                __stcs(reinterpret_cast<unsigned short*>(n + off(s, 0)), (unsigned short)(u & 0xffffu));
+                __stcs(reinterpret_cast<unsigned short*>(n + off(s, 0) + 64), (unsigned short)(u >> 16));
+            } else {
+                __stcs(reinterpret_cast<S*>(n + off(s, i)), Store<S>::put(d));
+            }
+        } else {
+            __stcs(reinterpret_cast<S*>(n + off(s, i)), d);
+        }
+    }
+    // the deviation a store of deviation d leaves in memory, as read back
+    static __device__ __forceinline__ T qdelta_d(int i, T d) {
+        if constexpr (PACKED) {
+            if (i > 0) return Store<S>::get(Store<S>::put(d));
+        }
+        return d;
+    }
     // store with an evict-first hint (streamed out, read only by the next step)
     static __device__ __forceinline__ void st_stream(unsigned char* n, int s, int i, T v) {
         if constexpr (PACKED) {
-            const T d = v - T(bias(s, i));
+            const double b = bias(s, i);
+            const T d = b == 0.0 ? v : v - T(b);
             if (i == 0) {
                 const unsigned u = __float_as_uint(d);
                 __stcs(reinterpret_cast<unsigned short*>(n + off(s, 0)), (unsigned short)(u & 0xffffu));
@@ -248,14 +283,17 @@ struct Fmt {
         }
     }
     static __device__ __forceinline__ void st(unsigned char* n, int s, int i, T v) {
-        st_delta(n, s, i, v - T(bias(s, i)));
+        const double b = bias(s, i);
+        st_delta(n, s, i, b == 0.0 ? v : v - T(b));
     }
     // the deviation a store of population value v leaves in memory, as read back
     static __device__ __forceinline__ T qdelta(int s, int i, T v) {
+        const double b = bias(s, i);
+        const T d = b == 0.0 ? v : v - T(b);
         if constexpr (PACKED) {
-            if (i > 0) return Store<S>::get(Store<S>::put(v - T(bias(s, i))));
+            if (i > 0) return Store<S>::get(Store<S>::put(d));
         }
-        return v - T(bias(s, i));
+        return d;
     }
 };
 
@@ -276,6 +314,14 @@ template <int Q, typename S>
 __device__ __forceinline__ void pst(void* base, const Geom& g, int s, int i, int x, int y, int z,
                                     typename Store<S>::T v) {
     Fmt<Q, S>::st(static_cast<unsigned char*>(base) + node_off<Q, S>(g, x, y, z), s, i, v);
+}
+
+// raw store (no rest-state offset): arrays in the population layout that hold
+// something other than populations (the adjoint's multipliers)
+template <int Q, typename S>
+__device__ __forceinline__ void pst_raw(void* base, const Geom& g, int s, int i, int x, int y, int z,
+                                        typename Store<S>::T v) {
+    Fmt<Q, S>::st_delta(static_cast<unsigned char*>(base) + node_off<Q, S>(g, x, y, z), s, i, v);
 }
 
 __device__ __forceinline__ int wrap(int v, int n) {
@@ -312,11 +358,13 @@ struct NodeEq {
     T rho, phi, psi;
     T ux, uy, uz;
     T bf, bg, bk;
+    T bf1;  // bf - 1, from rho - 1 without cancellation (when setup gets rd)
     T Gs[6];
 
-    // X = (rho, phi, psi), j = rho u, grad[X][a], lap[X]
+    // X = (rho, phi, psi), j = rho u, grad[X][a], lap[X]; rd = rho - 1 as summed
+    // from stored f deviations (the offset formats), used for bf1
     __host__ __device__ __forceinline__ void setup(const Phys<T>& P, T rho_, T jx, T jy, T jz, T phi_,
-                                          T psi_, const T (&grad)[3][3], const T (&lap)[3]) {
+                                          T psi_, const T (&grad)[3][3], const T (&lap)[3], T rd = T(0)) {
         rho = rho_; phi = phi_; psi = psi_;
         const T inv = T(1) / rho;
         ux = jx * inv; uy = jy * inv; uz = jz * inv;
@@ -326,14 +374,15 @@ struct NodeEq {
         const T lC[3] = {(lap[0] + lap[1] - lap[2]) * T(0.5), (lap[0] - lap[1] - lap[2]) * T(0.5),
                          lap[2]};
         T mu[3];
-        T pb = rho * T(1.0 / 3.0);
+        T pbx = T(0);  // p_b - rho c_s^2
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
             const T c = C[m];
             const T c1 = T(1) - c;
             mu[m] = P.kappa[m] * (c * c1 * (T(1) - T(2) * c) - P.a2 * lC[m]);
-            pb += P.kappa[m] * T(0.5) * c * c * c1 * (T(1) - T(3) * c);
+            pbx += P.kappa[m] * T(0.5) * c * c * c1 * (T(1) - T(3) * c);
         }
+        const T pb = rho * T(1.0 / 3.0) + pbx;
         const T mu_phi = (mu[0] - mu[1]) * T(0.5);
         const T mu_psi = mu[2] - (mu[0] + mu[1]) * T(0.5);
         // Laplacian part of the pressure tensor: L = sum_XY K_XY X lap Y
@@ -347,6 +396,7 @@ struct NodeEq {
             Lp += X[a] * s;
         }
         bf = T(3) * pb - T(3) * P.a2 * Lp - T(1.5) * rho * uu;
+        bf1 = (T(3) * pbx + rd) - T(3) * P.a2 * Lp - T(1.5) * rho * uu;
         bg = T(3) * P.gamma[0] * mu_phi - T(1.5) * phi * uu;
         bk = T(3) * P.gamma[1] * mu_psi - T(1.5) * psi * uu;
         // gradient part: G_ab = v_a^T K v_b with v_a = (d_a rho, d_a phi, d_a psi)

@@ -296,7 +296,7 @@ def test_tile_variants_are_bitwise_identical():
     n = 40
     C = W.spinodal((n, n, n), seed=8, amp=0.05)
     ref = None
-    for variant, chunk in ((0, 0), (1, 8), (2, 3), (3, 40), (1, 1), (4, 0), (5, 7), (6, 0), (7, 13), (8, 6)):
+    for variant, chunk in ((0, 0), (1, 8), (2, 3), (3, 40), (1, 1), (4, 0), (5, 7), (6, 0), (3, 13), (4, 6)):
         eng = tl.TernaryLB(19, n, n, n, (0.01, 0.01, 0.01), 1.0, 0.8, 0.1, 0.1, precision="fp32")
         eng.set_tile(variant, chunk)
         eng.init_fields(*W.to_aux(*C))
@@ -307,6 +307,22 @@ def test_tile_variants_are_bitwise_identical():
         else:
             assert np.array_equal(P, ref), (variant, chunk)
         eng.close()
+    # whole and single tiles along a, ragged b and marching extents
+    for shape in ((64, 21, 19), (32, 13, 11)):
+        nx, ny, nz = shape
+        C3 = W.spinodal((nz, ny, nx), seed=9, amp=0.05)
+        ref = None
+        for variant, chunk in ((0, 0), (5, 0), (6, 5), (3, 1), (4, 0)):
+            eng = tl.TernaryLB(19, nx, ny, nz, (0.01, 0.02, 0.015), 1.0, 0.8, 0.1, 0.1, precision="fp32")
+            eng.set_tile(variant, chunk)
+            eng.init_fields(*W.to_aux(*C3))
+            eng.step(6)
+            P = eng.get_populations()
+            if ref is None:
+                ref = P
+            else:
+                assert np.array_equal(P, ref), (shape, variant, chunk)
+            eng.close()
     C2 = W.spinodal((200, 300), seed=8, amp=0.05)
     ref = None
     for variant, chunk in ((0, 0), (1, 5), (2, 64), (3, 1)):
@@ -439,3 +455,33 @@ def test_launch_counts():
     assert eng2.kernel == "fused" and eng2.launches_per_step == 2
     eng2.set_kernel("split")
     assert eng2.launches_per_step == 4
+
+
+@pytest.mark.parametrize("Q,shape,walls", [(19, (37, 13, 11), False), (19, (37, 13, 11), True),
+                                           (9, (150, 37, 1), False), (9, (150, 37, 1), True)])
+def test_bounds_checked_step_records_nothing_and_matches(Q, shape, walls):
+    """The bounds-checked kernels (every population address against the buffer
+    and its chunk layout, every moment-ring and mask index against its extent)
+    record no violation on lattices ragged against the tiles, with and without
+    walls, and give bitwise the results of the unchecked kernels."""
+    nx, ny, nz = shape
+    sh = (ny, nx) if Q == 9 else (nz, ny, nx)
+    C = W.spinodal(sh, seed=12, amp=0.05)
+    solid = None
+    if walls:
+        solid = np.zeros(sh, dtype=np.uint8)
+        if Q == 9:
+            solid[0, :] = solid[-1, :] = 1
+            solid[9:15, 40:70] = 1
+        else:
+            solid[:, 0, :] = solid[:, -1, :] = 1
+            solid[3:7, 4:8, 10:20] = 1
+    out = []
+    for checked in (False, True):
+        eng, _, _ = _setup(Q, shape, C, "fp32", solid=solid, h=(0.0005, -0.0004, 0.0003))
+        eng.set_bounds_check(checked)
+        eng.step(5)
+        assert eng.bounds_check_word() == 0
+        out.append(eng.get_state())
+        eng.close()
+    assert np.array_equal(out[0], out[1])

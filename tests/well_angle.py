@@ -9,10 +9,12 @@ the walls (linear interpolation along the column); an algebraic circle fit
 (Pratt's normalisation, which also represents a straight line) is made to these
 points.  At each wall the fitted curve's point and tangent give the angle
 between the wall below the contact line (fluid 3's side) and the meniscus,
-i.e. theta_31 through fluid 3.  The contact line is "free" when it lies at
-least ``margin`` nodes from the well's floor and top corners on both walls;
-otherwise it is pinned at a corner or touching the floor and the angle is
-not a contact angle.
+i.e. theta_31 through fluid 3.  The meniscus is "free" when, on both walls,
+the C_3 = 1/2 crossing in the fluid column next to the wall (the contact line)
+and the fitted curve at the wall lie at least ``margin`` nodes from the well's
+floor and top, and its apex (the fitted curve at the well's centre) does too;
+otherwise it is pinned at a corner or touches the floor and the angle is not a
+contact angle.
 """
 import numpy as np
 
@@ -76,5 +78,21 @@ def meniscus_angle(C3, well, skip=3.0, margin=2.0, level=0.5):
         t /= np.hypot(*t)
         thetas.append(float(np.degrees(np.arccos(np.clip(-t[1], -1.0, 1.0)))))
         heights.append(float(yw))
-    free = all(y0 - 0.5 + margin <= h <= y1 - 0.5 - margin for h in heights)
+    xm = 0.5 * (x0 + x1) - 0.5
+    c = A * xm * xm + D * xm + F
+    if abs(A) < 1e-14:
+        apex = -c / E
+    else:
+        disc = E * E - 4 * A * c
+        apex = min(((-E + np.sqrt(disc)) / (2 * A), (-E - np.sqrt(disc)) / (2 * A)),
+                   key=lambda v: abs(v - ym)) if disc >= 0 else float("nan")
+    lo, hi = y0 - 0.5 + margin, y1 - 0.5 - margin
+    # contact line read directly in the fluid columns next to the walls
+    walls = []
+    for x in (x0, x1 - 1):
+        col = C3[y0:y1, x]
+        s = np.nonzero((col[:-1] >= level) & (col[1:] < level))[0]
+        walls.append(y0 + s[-1] + (col[s[-1]] - level) / (col[s[-1]] - col[s[-1] + 1]) if len(s) else float("nan"))
+    free = (all(lo <= h <= hi for h in heights) and all(lo <= h <= hi for h in walls)
+            and lo <= apex <= hi)
     return float(np.mean(thetas)), tuple(heights), free
