@@ -122,8 +122,16 @@ __host__ __device__ constexpr int stage_rank(int s, int i) {
     return sh ? s * 6 + is : 18 + s * 3 + iu;
 }
 
+// FP32 load through the non-coherent path with an L2 fetch size of 256 bytes:
+// a miss brings the neighbouring 128-byte run of the chunk into L2 as well.
+__device__ __forceinline__ float ld_l2x256(const unsigned char* p) {
+    float v;
+    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 template <int Q, typename S, int TX, int TY, bool ILP, bool EARLY, bool PF = false, int HINT = 0, int STG = 0,
-          int STGO = 1, bool CHK = false>
+          int STGO = 1, bool CHK = false, int LDH = 0>
 __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__ src, S* __restrict__ dst,
                                            const Phys<typename Store<S>::T>& P, double* __restrict__ partials,
                                            const int bid) {
@@ -197,8 +205,12 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
     const int nnodes = tid < NBORDER ? 2 : 1;
 
     const unsigned char* srcb = reinterpret_cast<const unsigned char*>(src);
-    // stored value (x - bias) of (s, i) at node pointer p
-    auto ldp = [&](const unsigned char* p, int s, int i) -> T { return Fmt<Q, S>::ld_delta(p, s, i); };
+    // stored value (x - bias) of (s, i) at node pointer p (LDH 1, FP32: with the
+    // 256-byte L2 fetch hint)
+    auto ldp = [&](const unsigned char* p, int s, int i) -> T {
+        if constexpr (LDH == 1 && sizeof(S) == 4) return ld_l2x256(p + Fmt<Q, S>::off(s, i));
+        else return Fmt<Q, S>::ld_delta(p, s, i);
+    };
     // pull source of direction (ca, cb, cm) for node n at plane rows zr
     auto src_of = [&](int n, const int (&zr)[3], int ca, int cb, int cm) -> const unsigned char* {
         const long long row = (long long)zr[1 - cm] * g.NB + yb[n][1 - cb];
@@ -451,11 +463,11 @@ k_fused(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename S
 // Variants of the periodic step with shared-memory staging of the pulled
 // populations (STG values in the order STGO), at BPS blocks per SM.
 template <int Q, typename S, int TX, int TY, int STG, int STGO, int BPS, bool ILP, bool PF, int HINT,
-          bool CHK = false>
+          bool CHK = false, int LDH = 0>
 __global__ void __launch_bounds__(TX * TY, BPS)
 k_fused_x(MGeom g, const S* __restrict__ src, S* __restrict__ dst, Phys<typename Store<S>::T> P,
           double* __restrict__ partials) {
-    fused_body<Q, S, TX, TY, ILP, false, PF, HINT, STG, STGO, CHK>(g, src, dst, P, partials, blockIdx.x);
+    fused_body<Q, S, TX, TY, ILP, false, PF, HINT, STG, STGO, CHK, LDH>(g, src, dst, P, partials, blockIdx.x);
 }
 
 // ------------------------------------------------------ solid-aware variant
@@ -880,11 +892,12 @@ struct FusedCfg {
 };
 
 // d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 shape 5,
-// D2Q9 128); D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4, 4..6 = 32x4 with the pulled
+// D2Q9 shape 5); D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4, 4..6 = 32x4 with the pulled
 // populations of a thread's node staged in shared memory for the collision
 // (4: the 19 f values; 5: lane-shifted values first, 28 for FP32, 19 with the
-// per-warp prefetch for 16-bit storage; 6: 19 lane-shifted values); D2Q9 1 =
-// 128, 2 = 256, 3 = 64.  mode (shapes 1..3 and D2Q9) bit 0: interleaved border
+// per-warp prefetch for 16-bit storage; 6: 19 lane-shifted values); D2Q9
+// shape 0 = 5: 128-node rows with all 27 values staged, 1 = 128, 2 = 256, 3 =
+// 64, 4 = 128 with the 18 lane-shifted values staged.  mode (shapes 1..3) bit 0: interleaved border
 // loads; bit 1: early phase-C loads; bit 2: per-warp L2 prefetch three planes
 // ahead; 8 / 9: evict-first stores / stores and collision loads (12, 13 with
 // the prefetch).  mode 0 is the default for the shape and format (D3Q19 32x4:
@@ -911,9 +924,10 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
         c.TY = v == 1 ? 8 : 4;
         c.shape = v;
     } else {
-        const int v = variant == 0 ? 1 : variant;
+        const int v = variant == 0 ? 5 : variant;  // 128-node rows with staging measured fastest
         c.TX = v == 2 ? 256 : (v == 3 ? 64 : 128);
         c.TY = 1;
+        c.shape = v;
     }
     c.mode = dbl ? 0 : ((tile >> 4) & 15);
     // defaults measured on GB300: D3Q19 32x4 with evict-first stores, plus a
@@ -978,18 +992,23 @@ inline int fused_partials(const tlbm_host::DevState& d, int kind) {
 // blocks per SM, so that the rest of the SM's 256 KB stays L1 (which holds the
 // kernel's loads in flight).
 template <typename K, typename... Args>
-inline cudaError_t launch_staged(K kern, int stg, long long nb, cudaStream_t st, Args... args) {
-    const int dyn = stg * 2 * 128 * (int)sizeof(float);
+inline cudaError_t launch_staged_t(K kern, int stg, int threads, int bps, long long nb, cudaStream_t st,
+                                   Args... args) {
+    const int dyn = stg * 2 * threads * (int)sizeof(float);
     cudaFuncAttributes fa{};
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
-    const long long need = 4LL * ((long long)fa.sharedSizeBytes + dyn + 1024);
+    const long long need = (long long)bps * ((long long)fa.sharedSizeBytes + dyn + 1024);
     const int pct = (int)((need * 100 + 233471) / 233472);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
     if (e != cudaSuccess) return e;
-    kern<<<(int)nb, 128, dyn, st>>>(args...);
+    kern<<<(int)nb, threads, dyn, st>>>(args...);
     return cudaSuccess;
+}
+template <typename K, typename... Args>
+inline cudaError_t launch_staged(K kern, int stg, long long nb, cudaStream_t st, Args... args) {
+    return launch_staged_t(kern, stg, 128, 4, nb, st, args...);
 }
 
 template <int Q, typename S>
@@ -1018,7 +1037,9 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
                                                         st, g, src, dst, P, d.partials);
                     if (e != cudaSuccess) return e;
                 } else {
-                    k_fused<Q, S, 128, 1, false, false, true, 2, true><<<(int)nb, 128, 0, st>>>(g, src, dst, P, d.partials);
+                    const cudaError_t e = launch_staged(k_fused_x<Q, S, 128, 1, 27, 0, 4, false, true, 2, true>, 27, nb,
+                                                        st, g, src, dst, P, d.partials);
+                    if (e != cudaSuccess) return e;
                 }
             }
             return cudaGetLastError();
@@ -1092,6 +1113,15 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
             else go(k_fused<Q, S, 32, 8, true, false>, 256);
         }
     } else {
+        if (c.shape >= 4 && !d.solid) {
+            // 128-node rows with staging: 4 the 18 lane-shifted values, 5 (default)
+            // all 27, with the per-warp prefetch and evict-first stores and
+            // collision loads
+            const cudaError_t e =
+                c.shape == 4 ? launch_staged(k_fused_x<Q, S, 128, 1, 18, 0, 4, false, true, 2>, 18, nb, st, g, src, dst, P, d.partials)
+                             : launch_staged(k_fused_x<Q, S, 128, 1, 27, 0, 4, false, true, 2>, 27, nb, st, g, src, dst, P, d.partials);
+            return e != cudaSuccess ? e : cudaGetLastError();
+        }
         if (c.TX == 256) {
             switch (c.mode) {
                 case 1: go(k_fused<Q, S, 256, 1, true, false>, 256); break;

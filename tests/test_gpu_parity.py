@@ -325,7 +325,7 @@ def test_tile_variants_are_bitwise_identical():
             eng.close()
     C2 = W.spinodal((200, 300), seed=8, amp=0.05)
     ref = None
-    for variant, chunk in ((0, 0), (1, 5), (2, 64), (3, 1)):
+    for variant, chunk in ((0, 0), (1, 5), (2, 64), (3, 1), (4, 0), (5, 3), (1, 0)):
         eng = tl.TernaryLB(9, 300, 200, 1, (0.01, 0.01, 0.01), 1.0, 0.8, 0.1, 0.1, precision="fp32")
         eng.set_tile(variant, chunk)
         eng.init_fields(*W.to_aux(*C2))

@@ -28,8 +28,9 @@ import numpy as np
 import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-if HERE not in sys.path:
-    sys.path.insert(0, HERE)
+for _p in (HERE, os.path.dirname(HERE)):
+    if _p not in sys.path:
+        sys.path.insert(0, _p)
 
 import paper_1511_02155_gb300 as tl  # noqa: E402
 from paper_1511_02155_gb300 import workloads as W  # noqa: E402
@@ -115,4 +116,4 @@ if __name__ == "__main__":
                           "within_4deg": int(np.sum(np.abs(err) <= BAND))}))
     for k, m in enumerate(members):
         print(json.dumps({"member": k, "nx": m["nx"], "well": m["well"], "young31": round(m["young31"], 3),
-                          **{f"theta_{T}": (round(res[T][k][0], 3), res[T][k][1]) for T in res}}))
+                          **{f"theta_{T}": (round(float(res[T][k][0]), 3), bool(res[T][k][1])) for T in res}}))
