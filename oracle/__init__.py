@@ -83,6 +83,12 @@ def _load():
             lib.orc_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp, dp,
                                         ctypes.POINTER(ctypes.c_int)]
             lib.orc_lattice.restype = ctypes.c_int
+            lib.orc_step_guo.argtypes = [pp, dp, dp, dp, ctypes.c_long]
+            lib.orc_step_guo.restype = ctypes.c_int
+            lib.orc_init_equilibrium_guo.argtypes = [pp, dp, dp, dp, dp, dp, dp]
+            lib.orc_init_equilibrium_guo.restype = ctypes.c_int
+            lib.orc_force.argtypes = [pp, dp, dp, dp, dp]
+            lib.orc_force.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -249,3 +255,39 @@ def wetting_gradients(p):
     G = np.zeros(3)
     lib.orc_wetting_gradients(ctypes.byref(p), _dp(G))
     return G
+
+
+# ----------------------------------------------------- forcing coupling (Guo)
+
+def step_guo(p, f, g, k, nsteps=1):
+    """Advance populations in place by nsteps steps of the forcing coupling
+    (periodic lattice; see the header of tlbm_oracle.c)."""
+    lib = _load()
+    rc = lib.orc_step_guo(ctypes.byref(p), _dp(f), _dp(g), _dp(k), int(nsteps))
+    if rc != 0:
+        raise RuntimeError(f"orc_step_guo failed ({rc})")
+    return f, g, k
+
+
+def init_equilibrium_guo(p, rho, phi, psi):
+    """Populations at the forcing coupling's equilibrium with the fields at rest."""
+    lib = _load()
+    N = _nodes(p)
+    f = np.zeros((p.Q, N)); g = np.zeros((p.Q, N)); k = np.zeros((p.Q, N))
+    a = [np.ascontiguousarray(x, dtype=np.float64).reshape(N) for x in (rho, phi, psi)]
+    rc = lib.orc_init_equilibrium_guo(ctypes.byref(p), *[_dp(x) for x in a], _dp(f), _dp(g), _dp(k))
+    if rc != 0:
+        raise RuntimeError(f"orc_init_equilibrium_guo failed ({rc})")
+    return f, g, k
+
+
+def force(p, rho, phi, psi):
+    """Body force [3][N] = -(rho grad mu_rho + phi grad mu_phi + psi grad mu_psi)."""
+    lib = _load()
+    N = _nodes(p)
+    a = [np.ascontiguousarray(x, dtype=np.float64).reshape(N) for x in (rho, phi, psi)]
+    F = np.zeros((3, N))
+    rc = lib.orc_force(ctypes.byref(p), *[_dp(x) for x in a], _dp(F))
+    if rc != 0:
+        raise RuntimeError(f"orc_force failed ({rc})")
+    return F

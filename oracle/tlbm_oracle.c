@@ -28,6 +28,24 @@
  *                        at solid nodes ("standard bounce back")
  *   O8 mass totals       Kahan-summed sums of rho, phi, psi over fluid nodes
  *
+ * The forcing coupling (orc_step_guo), the alternative that Sec. Equations of
+ * Motion mentions beside the pressure-tensor route (Guo forcing): the
+ * thermodynamic terms enter the momentum equation as a body force.  In the
+ * continuum it is F = -(rho grad mu_rho + phi grad mu_phi + psi grad mu_psi),
+ * the last three
+ * terms of the Navier-Stokes equation, which the paper writes as the divergence
+ * of its pressure tensor minus the ideal-gas pressure; on the lattice it is
+ * taken in that divergence form,
+ *   F_a = -d_b (P_ab - rho c_s^2 delta_ab),
+ * P_ab node by node from O3-O4 (the printed pressure tensor, with p_b, alpha^2
+ * and the symmetric cross terms read as listed below)
+ * and d_b by the isotropic gradient stencil of O3, so that the total momentum
+ * is conserved exactly on a periodic lattice.  f relaxes to the ideal-gas
+ * equilibrium (pressure rho c_s^2) at u = (rho v + F/2) / rho and receives the
+ * source of Guo, Zheng and Shi (2002):
+ *   (1 - 1/(2 tau)) w_i [(e_i - u).F / c_s^2 + (e_i.u)(e_i.F) / c_s^4];
+ * g and k keep their equilibria, evaluated at the same u.  Periodic lattices.
+ *
  * Readings taken where the paper is silent or misprinted (each pinned by a test):
  *   - mu_rho is the functional derivative dF/drho, i.e. (mu_1 + mu_2)/2; the
  *     printed mu_rho has a sign and a Laplacian mix-up.  mu_phi and mu_psi match
@@ -578,4 +596,207 @@ void orc_mass(const orc_params *p, const uint8_t *solid, const double *f, const 
         }
         out[c] = s;
     }
+}
+
+/* ---------------------------------------------------- forcing coupling (Guo) */
+
+/* Chemical potentials (mu_rho, mu_phi, mu_psi) [3][N] of fields X at every node. */
+static void chemical_potentials(const orc_params *p, const lattice *L, const double *rho, const double *phi,
+                                const double *psi, double *mu)
+{
+    const size_t N = L->N;
+    const double *F[3] = {rho, phi, psi};
+#pragma omp parallel for schedule(static)
+    for (long rr = 0; rr < (long)N; ++rr) {
+        const size_t r = (size_t)rr;
+        double X[3] = {rho[r], phi[r], psi[r]}, lap[3], gr[3], C[3], m[3], pb;
+        for (int c = 0; c < 3; ++c) derivs_at(L, F[c], r, gr, &lap[c]);
+        orc_thermo_node(p, X, lap, C, m, &pb);
+        for (int c = 0; c < 3; ++c) mu[(size_t)c * N + r] = m[c];
+    }
+}
+
+/* Non-ideal part of the pressure tensor, P_ab - rho c_s^2 delta_ab, at one node
+ * (Sec. Equations of Motion, with the p_b, alpha^2 and cross-term readings of
+ * the header), components xx yy zz xy yz zx. */
+static void nonideal_pressure(const orc_params *p, const double X[3], const double grad[3][3],
+                              const double lap[3], double Pi[6])
+{
+    const double a2 = p->alpha * p->alpha;
+    double C[3], mu[3], pb;
+    orc_thermo_node(p, X, lap, C, mu, &pb);
+    double K[3][3];
+    mixing(p, K);
+    static const int ca[6] = {0, 1, 2, 0, 1, 2};
+    static const int cb[6] = {0, 1, 2, 1, 2, 0};
+    /* isotropic part: p_b - rho/3 - alpha^2 [sum_X K_XX (|grad X|^2 / 2 + X lap X)
+     *   + sum_{X<Y} K_XY (grad X . grad Y + X lap Y + Y lap X)] */
+    double iso = pb - X[0] / 3.0;
+    for (int x = 0; x < 3; ++x) {
+        const double g2 = grad[x][0] * grad[x][0] + grad[x][1] * grad[x][1] + grad[x][2] * grad[x][2];
+        iso -= a2 * K[x][x] * (0.5 * g2 + X[x] * lap[x]);
+        for (int y = x + 1; y < 3; ++y) {
+            const double gg = grad[x][0] * grad[y][0] + grad[x][1] * grad[y][1] + grad[x][2] * grad[y][2];
+            iso -= a2 * K[x][y] * (gg + X[x] * lap[y] + X[y] * lap[x]);
+        }
+    }
+    for (int c = 0; c < 6; ++c) {
+        const int al = ca[c], be = cb[c];
+        double s = 0.0;
+        for (int x = 0; x < 3; ++x) {
+            s += K[x][x] * grad[x][al] * grad[x][be];
+            for (int y = x + 1; y < 3; ++y) s += K[x][y] * (grad[x][al] * grad[y][be] + grad[y][al] * grad[x][be]);
+        }
+        Pi[c] = a2 * s + (c < 3 ? iso : 0.0);
+    }
+}
+
+/* Body force F [3][N] = -div (P - rho c_s^2 I) of the fields rho, phi, psi
+ * (periodic lattice). */
+static void force_field(const orc_params *p, const lattice *L, const double *rho, const double *phi,
+                        const double *psi, double *Pi, double *F)
+{
+    const size_t N = L->N;
+    const double *X3[3] = {rho, phi, psi};
+#pragma omp parallel for schedule(static)
+    for (long rr = 0; rr < (long)N; ++rr) {
+        const size_t r = (size_t)rr;
+        double X[3] = {rho[r], phi[r], psi[r]}, grad[3][3], lap[3], P6[6];
+        for (int c = 0; c < 3; ++c) derivs_at(L, X3[c], r, grad[c], &lap[c]);
+        nonideal_pressure(p, X, (const double (*)[3])grad, lap, P6);
+        for (int c = 0; c < 6; ++c) Pi[(size_t)c * N + r] = P6[c];
+    }
+    /* component (a, b) of the symmetric tensor in the xx yy zz xy yz zx order */
+    static const int comp[3][3] = {{0, 3, 5}, {3, 1, 4}, {5, 4, 2}};
+#pragma omp parallel for schedule(static)
+    for (long rr = 0; rr < (long)N; ++rr) {
+        const size_t r = (size_t)rr;
+        for (int a = 0; a < 3; ++a) {
+            double div = 0.0;
+            for (int b = 0; b < 3; ++b) {
+                double gb[3], lb;
+                derivs_at(L, Pi + (size_t)comp[a][b] * N, r, gb, &lb);
+                div += gb[b];
+            }
+            F[(size_t)a * N + r] = -div;
+        }
+    }
+}
+
+int orc_force(const orc_params *p, const double *rho, const double *phi, const double *psi, double *F)
+{
+    lattice L;
+    if (lattice_init(&L, p) != 0) return -1;
+    double *Pi = calloc(6 * L.N, sizeof(double));
+    if (!Pi) return -2;
+    force_field(p, &L, rho, phi, psi, Pi, F);
+    free(Pi);
+    return 0;
+}
+
+/* Equilibria of the forcing coupling at one node: ideal-gas f_eq at velocity u,
+ * g_eq and k_eq with mu_phi, mu_psi; directions i >= 1 from the formulas, i = 0
+ * from the mass constraints. */
+static void equilibrium_guo(const orc_params *p, const lattice *L, const double X[3], const double u[3],
+                            const double mu[3], double *feq, double *geq, double *keq)
+{
+    const double cs2 = 1.0 / 3.0;
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double sf = 0.0, sg = 0.0, sk = 0.0;
+    for (int i = 1; i < L->Q; ++i) {
+        double eu = 0.0;
+        for (int a = 0; a < 3; ++a) eu += L->e[i][a] * u[a];
+        const double quad = (eu * eu - cs2 * uu) / (2.0 * cs2 * cs2);
+        const double wi = L->w[i];
+        feq[i] = wi * X[0] * (1.0 + eu / cs2 + quad);
+        geq[i] = wi * (p->gamma[0] * mu[1] / cs2 + X[1] * eu / cs2 + X[1] * quad);
+        keq[i] = wi * (p->gamma[1] * mu[2] / cs2 + X[2] * eu / cs2 + X[2] * quad);
+        sf += feq[i]; sg += geq[i]; sk += keq[i];
+    }
+    feq[0] = X[0] - sf;
+    geq[0] = X[1] - sg;
+    keq[0] = X[2] - sk;
+}
+
+/* Advance populations f, g, k ([Q][N] each, periodic lattice) by nsteps time
+ * steps of the forcing coupling. */
+int orc_step_guo(const orc_params *p, double *f, double *g, double *k, long nsteps)
+{
+    lattice L;
+    if (lattice_init(&L, p) != 0) return -1;
+    const size_t N = L.N;
+    work w;
+    double *mu = calloc(3 * N, sizeof(double)), *Pi = calloc(6 * N, sizeof(double)),
+           *F = calloc(3 * N, sizeof(double));
+    if (work_alloc(&w, N, L.Q) != 0 || !mu || !Pi || !F) {
+        work_free(&w); free(mu); free(Pi); free(F);
+        return -2;
+    }
+    const double cs2 = 1.0 / 3.0;
+    for (long t = 0; t < nsteps; ++t) {
+        orc_moments(p, NULL, f, g, k, w.rho, w.jx, w.jy, w.jz, w.phi, w.psi);
+        chemical_potentials(p, &L, w.rho, w.phi, w.psi, mu);
+        force_field(p, &L, w.rho, w.phi, w.psi, Pi, F);
+#pragma omp parallel for schedule(static)
+        for (long rr = 0; rr < (long)N; ++rr) {
+            const size_t r = (size_t)rr;
+            const double X[3] = {w.rho[r], w.phi[r], w.psi[r]};
+            const double m[3] = {mu[r], mu[N + r], mu[2 * N + r]};
+            const double Fr[3] = {F[r], F[N + r], F[2 * N + r]};
+            const double j[3] = {w.jx[r], w.jy[r], w.jz[r]};
+            double u[3];
+            for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * Fr[a]) / X[0];
+            double feq[19], geq[19], keq[19];
+            equilibrium_guo(p, &L, X, u, m, feq, geq, keq);
+            const double pref = 1.0 - 1.0 / (2.0 * p->tau[0]);
+            for (int i = 0; i < L.Q; ++i) {
+                double eu = 0.0, eF = 0.0, uF = 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    eu += L.e[i][a] * u[a];
+                    eF += L.e[i][a] * Fr[a];
+                    uF += u[a] * Fr[a];
+                }
+                const double Si = pref * L.w[i] * ((eF - uF) / cs2 + eu * eF / (cs2 * cs2));
+                const size_t o = (size_t)i * N + r;
+                w.fs[o] = f[o] - (f[o] - feq[i]) / p->tau[0] + Si;
+                w.gs[o] = g[o] - (g[o] - geq[i]) / p->tau[1];
+                w.ks[o] = k[o] - (k[o] - keq[i]) / p->tau[2];
+            }
+        }
+        orc_stream(p, NULL, w.fs, f);
+        orc_stream(p, NULL, w.gs, g);
+        orc_stream(p, NULL, w.ks, k);
+    }
+    work_free(&w);
+    free(mu); free(Pi); free(F);
+    return 0;
+}
+
+/* Populations at the forcing coupling's equilibrium with the given fields at
+ * rest (periodic lattice): f_eq at u = 0, g_eq and k_eq with mu. */
+int orc_init_equilibrium_guo(const orc_params *p, const double *rho, const double *phi, const double *psi,
+                             double *f, double *g, double *k)
+{
+    lattice L;
+    if (lattice_init(&L, p) != 0) return -1;
+    const size_t N = L.N;
+    double *mu = calloc(3 * N, sizeof(double));
+    if (!mu) return -2;
+    chemical_potentials(p, &L, rho, phi, psi, mu);
+    const double u0[3] = {0.0, 0.0, 0.0};
+#pragma omp parallel for schedule(static)
+    for (long rr = 0; rr < (long)N; ++rr) {
+        const size_t r = (size_t)rr;
+        const double X[3] = {rho[r], phi[r], psi[r]};
+        const double m[3] = {mu[r], mu[N + r], mu[2 * N + r]};
+        double feq[19], geq[19], keq[19];
+        equilibrium_guo(p, &L, X, u0, m, feq, geq, keq);
+        for (int i = 0; i < L.Q; ++i) {
+            f[(size_t)i * N + r] = feq[i];
+            g[(size_t)i * N + r] = geq[i];
+            k[(size_t)i * N + r] = keq[i];
+        }
+    }
+    free(mu);
+    return 0;
 }
