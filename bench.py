@@ -13,7 +13,13 @@ lattice and reports them under "companions" (MLUPS, kernel time, roofline
 fractions, largest |dC_m| against the FP32 run after the same steps).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload spinodal256|lens512|probe8192] [--precision fp32|fp64|fp16|bf16]
+                  [--workload spinodal256|lens512|probe8192|wells4096|sweep96]
+                  [--precision fp32|fp64|fp16|bf16] [--coupling pressure_tensor|forcing]
+
+--coupling forcing times the Guo body-force coupling (three kernels per step:
+moments, pressure tensor and chemical potentials, collide+stream) on the
+periodic workloads; its roofline keeps the algorithmic 1 read + 1 write of the
+populations per node, so the fraction is against the ideal one-pass step.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload on
 its own GPU (weak scaling, no collective in the data path); timing takes the
@@ -426,6 +432,8 @@ def main():
                     choices=["spinodal256", "lens512", "probe8192", "wells4096", "sweep96"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16", "bf16"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "split"])
+    ap.add_argument("--coupling", default="pressure_tensor", choices=["pressure_tensor", "forcing"],
+                    help="forcing: the Guo body-force coupling (periodic workloads, split kernels)")
     ap.add_argument("--tile", default="0,0")
     ap.add_argument("--size", type=int, default=0, help="lattice edge override (profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -477,7 +485,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    with_companions = (args.precision == "fp32" and args.workload == "spinodal256" and not args.no_companions)
+    if args.coupling == "forcing" and solid is not None:
+        raise SystemExit("--coupling forcing runs on periodic workloads only")
+    with_companions = (args.precision == "fp32" and args.workload == "spinodal256" and not args.no_companions
+                       and args.coupling == "pressure_tensor")
     main_run = measure(args, cfg, fields, solid, args.precision, args.tile, args.kernel, world, local, dist,
                        barrier, keep_fields=with_companions)
     value, ms, clocks, m_after = main_run["value"], main_run["ms"], main_run["clocks"], main_run["mass"]
@@ -490,6 +501,8 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     tag = f"{kind}:{args.workload}:{args.precision}:{args.tile}"
+    if args.coupling != "pressure_tensor":
+        tag += f":{args.coupling}"
     traffic = traffic_from_profiles(tag, kernel_source_digest(), N)
 
     # the 16-bit storage companions of the FP32 headline (the metric compares
@@ -525,7 +538,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": label, "nodes_per_gpu": N, "fluid_nodes_per_gpu": n_fluid,
                        "lattice": f"D{3 if Q == 19 else 2}Q{Q}",
-                       "precision": args.precision, "kernel": kind,
+                       "precision": args.precision, "kernel": kind, "coupling": args.coupling,
                        "l2": "populations exceed L2 (no flush needed)" if alg_bytes / 2 > 129e6
                        else "L2-resident lattice", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -564,6 +577,8 @@ def measure(args, cfg, fields, solid, precision, tile, kernel, world, local, dis
                        cfg["M_psi"], cfg["h"], solid, precision)
     if kernel != "auto":
         eng.set_kernel(kernel)
+    if getattr(args, "coupling", "pressure_tensor") != "pressure_tensor":
+        eng.set_coupling(args.coupling)
     tv, tc = (int(v) for v in tile.split(","))
     eng.set_tile(tv, tc)
     eng.init_fields(rho, phi, psi)

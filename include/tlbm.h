@@ -374,6 +374,37 @@ void tlbm_batch_destroy(tlbm_batch *b);
 tlbm_status tlbm_set_bounds_check(tlbm *t, int on);
 tlbm_status tlbm_bounds_check_word(tlbm *t, uint64_t *word);
 
+/*
+ * How the thermodynamic force enters the momentum equation (Sec. Equations of
+ * Motion offers both routes).
+ *   TLBM_COUPLING_PRESSURE_TENSOR: the paper's default: the second moment of
+ *       f_eq is the full pressure tensor P_ab (every kernel kind).
+ *   TLBM_COUPLING_FORCING: Guo forcing: f_eq is the ideal-gas equilibrium and
+ *       the body force F_a = -d_b (P_ab - rho c_s^2 delta_ab), the divergence of
+ *       the same tensor's non-ideal part by the isotropic gradient stencil,
+ *       enters through the source of Guo, Zheng and Shi (2002) at the fluid
+ *       velocity u = (j + F/2)/rho.  In the continuum F = -(rho grad mu_rho +
+ *       phi grad mu_phi + psi grad mu_psi); on the lattice sum_r F = 0 exactly.
+ *       g and k are unchanged.  Three kernels per step (moments; Pi_ab, mu_phi,
+ *       mu_psi arrays; collide+stream); no fused kernel.
+ */
+typedef enum { TLBM_COUPLING_PRESSURE_TENSOR = 0, TLBM_COUPLING_FORCING = 1 } tlbm_coupling;
+
+/*
+ * Select the coupling.  TLBM_COUPLING_FORCING needs a lattice without solid
+ * nodes and an engine whose kernel choice is not TLBM_KERNEL_FUSED
+ * (TLBM_ERR_UNSUPPORTED otherwise); it allocates (NPI + 2) node arrays of the
+ * compute type, NPI = 3 on D2Q9 and 6 on D3Q19 (TLBM_ERR_OOM if that fails),
+ * which tlbm_destroy frees.  The populations are left as they are: call
+ * tlbm_init_fields afterwards to start from the coupling's own equilibrium
+ * (under forcing, the u given there is the stored momentum over rho; the
+ * fluid velocity adds F/(2 rho)).  Under forcing, tlbm_fields returns the
+ * fluid velocity (j + F/2)/rho, and batches and the adjoint refuse the engine
+ * (TLBM_ERR_UNSUPPORTED).  tlbm_step_noalloc always uses the pressure tensor.
+ */
+tlbm_status tlbm_set_coupling(tlbm *t, tlbm_coupling coupling);
+tlbm_coupling tlbm_get_coupling(const tlbm *t);
+
 /* Message of the last failed tlbm_step_noalloc call on this host thread ("" if none). */
 const char *tlbm_noalloc_last_error(void);
 

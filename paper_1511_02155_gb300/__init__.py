@@ -22,11 +22,15 @@ import numpy as np
 
 __all__ = ["TernaryLB", "TernaryBatch", "TLBMError", "contact_angles", "wetting_from_angles", "load_library", "lib_path", "D2Q9", "D3Q19",
            "FP64", "FP32", "FP16_OFFSET", "BF16_OFFSET", "KERNEL_AUTO", "KERNEL_FUSED",
-           "KERNEL_SPLIT"]
+           "KERNEL_SPLIT", "COUPLING_PRESSURE_TENSOR", "COUPLING_FORCING"]
 
 D2Q9, D3Q19 = 9, 19
 FP64, FP32, FP16_OFFSET, BF16_OFFSET = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_FUSED, KERNEL_SPLIT = 0, 1, 2
+COUPLING_PRESSURE_TENSOR, COUPLING_FORCING = 0, 1
+_COUPLING = {"pressure_tensor": COUPLING_PRESSURE_TENSOR, "forcing": COUPLING_FORCING,
+             "guo": COUPLING_FORCING, COUPLING_PRESSURE_TENSOR: COUPLING_PRESSURE_TENSOR,
+             COUPLING_FORCING: COUPLING_FORCING}
 _PREC = {"fp64": FP64, "fp32": FP32, "fp16": FP16_OFFSET, "bf16": BF16_OFFSET,
          FP64: FP64, FP32: FP32, FP16_OFFSET: FP16_OFFSET, BF16_OFFSET: BF16_OFFSET}
 _KIND = {"auto": KERNEL_AUTO, "fused": KERNEL_FUSED, "split": KERNEL_SPLIT,
@@ -65,6 +69,8 @@ def _declare(lib):
         "tlbm_set_kernel": (i, [_H, i]),
         "tlbm_get_kernel": (i, [_H]),
         "tlbm_set_tile": (i, [_H, i, i]),
+        "tlbm_set_coupling": (i, [_H, i]),
+        "tlbm_get_coupling": (i, [_H]),
         "tlbm_set_bounds_check": (i, [_H, i]),
         "tlbm_bounds_check_word": (i, [_H, ctypes.POINTER(ctypes.c_uint64)]),
         "tlbm_init_fields": (i, [_H, _dp, _dp, _dp, _dp, _dp, _dp]),
@@ -213,6 +219,16 @@ class TernaryLB:
     @property
     def launches_per_step(self):
         return int(self._lib.tlbm_launches_per_step(self._h))
+
+    def set_coupling(self, coupling):
+        """'pressure_tensor' (the default) or 'forcing' (Guo body force; periodic
+        lattices, three kernels per step).  Call init_fields afterwards."""
+        self._check(self._lib.tlbm_set_coupling(self._h, _COUPLING[coupling]))
+
+    @property
+    def coupling(self):
+        return {COUPLING_PRESSURE_TENSOR: "pressure_tensor",
+                COUPLING_FORCING: "forcing"}[self._lib.tlbm_get_coupling(self._h)]
 
     def set_bounds_check(self, on=True):
         """Run the bounds-checked variants of the fused step (FP32 storage)."""

@@ -157,6 +157,7 @@ void tlbm_destroy(tlbm* t) {
     cudaFree((void*)t->d.solid);
     cudaFree(t->d.nbm);
     cudaFree(t->d.mom);
+    cudaFree(t->d.aux);
     cudaFree(t->d.partials);
     cudaFree(t->d.step_mass);
     cudaFree(t->d.mass_tmp);
@@ -327,6 +328,29 @@ tlbm_status tlbm_set_tile(tlbm* t, int variant, int chunk) {
     t->d.tile = variant + 256 * chunk;
     // partial sums must fit: blocks grow as chunks shrink
     return TLBM_OK;
+}
+
+tlbm_status tlbm_set_coupling(tlbm* t, tlbm_coupling coupling) {
+    if (!t) return TLBM_ERR_ARG;
+    if (coupling != TLBM_COUPLING_PRESSURE_TENSOR && coupling != TLBM_COUPLING_FORCING)
+        return fail(t, TLBM_ERR_ARG, "unknown coupling");
+    if (coupling == TLBM_COUPLING_FORCING) {
+        if (t->d.solid)
+            return fail(t, TLBM_ERR_UNSUPPORTED, "the forcing coupling runs on lattices without solid nodes");
+        if (t->kind_req == TLBM_KERNEL_FUSED)
+            return fail(t, TLBM_ERR_UNSUPPORTED,
+                        "the fused kernels carry the pressure-tensor coupling only; select TLBM_KERNEL_AUTO or SPLIT");
+        tlbm_status s = ensure_mom(t);
+        if (s != TLBM_OK) return s;
+        if (!t->d.aux)
+            CK(cudaMalloc(&t->d.aux, t->tsize * (size_t)t->ops->aux_per_node() * (size_t)t->d.Np));
+    }
+    t->d.coupling = coupling == TLBM_COUPLING_FORCING ? 1 : 0;
+    return TLBM_OK;
+}
+
+tlbm_coupling tlbm_get_coupling(const tlbm* t) {
+    return t && t->d.coupling ? TLBM_COUPLING_FORCING : TLBM_COUPLING_PRESSURE_TENSOR;
 }
 
 tlbm_status tlbm_set_bounds_check(tlbm* t, int on) {
@@ -532,6 +556,8 @@ tlbm_status tlbm_adjoint_c3_misfit(tlbm* t, int64_t nsteps, int checkpoint_every
     if (!target || !loss || !dkappa || !dh) return fail(t, TLBM_ERR_ARG, "target, loss, dkappa and dh are required");
     if (t->d.prec != TLBM_FP64 && t->d.prec != TLBM_FP32)
         return fail(t, TLBM_ERR_UNSUPPORTED, "the adjoint needs TLBM_FP64 or TLBM_FP32 storage");
+    if (t->d.coupling)
+        return fail(t, TLBM_ERR_UNSUPPORTED, "the adjoint differentiates the pressure-tensor coupling only");
     if (!t->rest_init || t->steps != 0)
         return fail(t, TLBM_ERR_ARG,
                     "the adjoint starts from the state of tlbm_init_fields with u = NULL and no step since");
@@ -652,6 +678,9 @@ tlbm_status batch_rebuild(tlbm_batch* b) {
 // members at one buffer parity, with the parameters the descriptors hold
 // (rebuilt when tlbm_set_gamma changed a member since)
 tlbm_status batch_aligned(tlbm_batch* b) {
+    for (size_t k = 0; k < b->sims.size(); ++k)
+        if (b->sims[k]->coupling)
+            return bfail(b, TLBM_ERR_UNSUPPORTED, "member %zu uses the forcing coupling (no batched kernel)", k);
     for (size_t k = 1; k < b->sims.size(); ++k)
         if (b->sims[k]->cur != b->sims[0]->cur)
             return bfail(b, TLBM_ERR_ARG, "batch members are at different step parities (a member was stepped alone)");
@@ -696,6 +725,8 @@ tlbm_status tlbm_batch_create(tlbm_batch** out, tlbm* const* members, int count)
             return bfail(nullptr, TLBM_ERR_ARG, "members must share the device and stream");
         if ((m->d.solid != nullptr) != (m0->d.solid != nullptr))
             return bfail(nullptr, TLBM_ERR_ARG, "members must all have, or all lack, solid nodes");
+        if (m->d.coupling)
+            return bfail(nullptr, TLBM_ERR_UNSUPPORTED, "member %d uses the forcing coupling (no batched kernel)", k);
         for (int j = 0; j < k; ++j)
             if (members[j] == m) return bfail(nullptr, TLBM_ERR_ARG, "member %d appears twice", k);
     }

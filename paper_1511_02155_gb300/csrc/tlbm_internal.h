@@ -54,6 +54,8 @@ struct DevState {
     unsigned long long* check;  // device word: first bounds violation of a checked step
     int checked;         // 1: the fused step runs its bounds-checked kernels
     long long partials_cap;  // blocks whose partial sums fit in the first part of partials
+    int coupling;        // 0: pressure-tensor equilibrium; 1: forcing (Guo) coupling
+    void* aux;           // forcing coupling's node arrays [NA][Np] (compute type)
 };
 
 // A batch of engines of one lattice and storage format, advanced together by
@@ -97,6 +99,8 @@ struct Ops {
                            cudaStream_t st);
     cudaError_t (*set_pops)(DevState& d, const double* in, cudaStream_t st);
     int (*launches)(const DevState& d, int kind);
+    // compute-type values per node of the forcing coupling's node arrays
+    int (*aux_per_node)();
     bool (*has_fused)(const DevState& d);
     // batches: build the descriptors of both parities (and neighbour masks);
     // one step of every member (flips every member's cur)

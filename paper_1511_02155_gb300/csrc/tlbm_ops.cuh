@@ -4,6 +4,7 @@
 
 #include "tlbm_adjoint.cuh"
 #include "tlbm_fused.cuh"
+#include "tlbm_guo.cuh"
 #include "tlbm_kernels.cuh"
 
 namespace tlbm_dev {
@@ -38,9 +39,32 @@ struct Impl {
         k_collide_split<Q, S, SOLID><<<grid, kThreads, 0, st>>>(g, src, dst, d.solid, mom, P);
     }
 
+    // moments of src into mom (block partials into part) and the forcing
+    // coupling's Pi, mu_phi, mu_psi into aux
+    static void guo_aux(DevState& d, const S* src, double* part, cudaStream_t st) {
+        const Geom g = geom(d);
+        T* mom = static_cast<T*>(d.mom);
+        k_moments<Q, S, false, true><<<kMassBlocks, kThreads, 0, st>>>(g, src, nullptr, mom, part);
+        k_guo_pressure<Q, T><<<grid_for(g.N, d.sms), kThreads, 0, st>>>(g, mom, static_cast<T*>(d.aux),
+                                                                         to_phys<T>(d.phys));
+    }
+
+    static void guo(DevState& d, cudaStream_t st) {
+        const S* src = static_cast<const S*>(d.pop[d.cur]);
+        guo_aux(d, src, d.partials, st);
+        const Geom g = geom(d);
+        k_guo_collide<Q, S><<<grid_for(g.N, d.sms), kThreads, 0, st>>>(
+            g, src, static_cast<S*>(d.pop[1 - d.cur]), static_cast<const T*>(d.aux), to_phys<T>(d.phys));
+    }
+
+    static int aux_per_node() { return GuoAux<Q>::NA; }
+
     static cudaError_t step(DevState& d, int kind, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
+        if (d.coupling) kind = tlbm_host::KIND_SPLIT;  // the fused kernels carry the pressure tensor only
         if (ev0) cudaEventRecord(ev0, st);
-        if (kind == tlbm_host::KIND_FUSED) {
+        if (d.coupling) {
+            guo(d, st);
+        } else if (kind == tlbm_host::KIND_FUSED) {
             cudaError_t e = fused_step<Q, S>(d, to_phys<T>(d.phys), st);
             if (e != cudaSuccess) return e;
         } else {
@@ -62,7 +86,11 @@ struct Impl {
         S* dst = static_cast<S*>(d.pop[d.cur]);
         const int grid = grid_for(g.N, d.sms);
         k_fields_to_mom<T><<<grid, kThreads, 0, st>>>(g, rho, phi, psi, d.solid, mom);
-        if (d.solid) {
+        if (d.coupling) {
+            T* aux = static_cast<T*>(d.aux);
+            k_guo_pressure<Q, T><<<grid, kThreads, 0, st>>>(g, mom, aux, P);
+            k_guo_init<Q, S><<<grid, kThreads, 0, st>>>(g, dst, mom, aux, u, P);
+        } else if (d.solid) {
             k_ghosts<Q, T><<<grid, kThreads, 0, st>>>(g, d.solid, mom, P);
             k_init_eq<Q, S, true><<<grid, kThreads, 0, st>>>(g, dst, d.solid, mom, u, P);
         } else {
@@ -78,6 +106,12 @@ struct Impl {
         const int grid = grid_for(g.N, d.sms);
         if (d.solid) k_fields<Q, S, true><<<grid, kThreads, 0, st>>>(g, src, d.solid, C1, C2, C3, rho, u);
         else k_fields<Q, S, false><<<grid, kThreads, 0, st>>>(g, src, d.solid, C1, C2, C3, rho, u);
+        if (d.coupling && u) {
+            // fluid velocity (j + F/2) / rho of the forcing coupling
+            guo_aux(d, src, d.partials + 3 * d.partials_cap, st);
+            k_guo_velocity<Q, T><<<grid, kThreads, 0, st>>>(g, static_cast<const T*>(d.mom),
+                                                             static_cast<const T*>(d.aux), u);
+        }
         return cudaGetLastError();
     }
 
@@ -115,11 +149,12 @@ struct Impl {
     }
 
     static int launches(const DevState& d, int kind) {
+        if (d.coupling) return 3 + 1;
         if (kind == tlbm_host::KIND_FUSED) return fused_launches<Q, S>(d) + 1;
         return (d.solid ? 3 : 2) + 1;
     }
 
-    static bool has_fused(const DevState& d) { return fused_supported<Q, S>(d); }
+    static bool has_fused(const DevState& d) { return !d.coupling && fused_supported<Q, S>(d); }
 
     template <bool SOLID>
     static cudaError_t adjoint_run(DevState& d, int kind, const tlbm_host::AdjJob& J, cudaStream_t st) {
@@ -215,8 +250,9 @@ struct Impl {
     }
 
     static const tlbm_host::Ops* table() {
-        static const tlbm_host::Ops o = {&step,     &init,      &fields, &mass,  &get_box, &set_pops,
-                                         &launches, &has_fused, &bbuild, &bstep, &adjoint};
+        static const tlbm_host::Ops o = {&step,     &init,         &fields,    &mass,   &get_box,
+                                         &set_pops, &launches,     &aux_per_node, &has_fused, &bbuild,
+                                         &bstep,    &adjoint};
         return &o;
     }
 };
