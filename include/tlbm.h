@@ -367,8 +367,10 @@ void tlbm_batch_destroy(tlbm_batch *b);
  * source, 2 bounce-back source, 3 store target, 4 moment-ring index, 5 mask
  * index; the access is redirected to a valid address and the kernel carries on
  * (no trap, no fault).  The checked kernels use the default tile and compute
- * the same results as the unchecked ones.  TLBM_ERR_UNSUPPORTED for other
- * storage formats.  tlbm_bounds_check_word waits for the engine's stream,
+ * the same results as the unchecked ones.  The checked kernels are those of
+ * the pressure-tensor coupling (an engine under TLBM_COUPLING_FORCING runs its
+ * unchecked kernels).  TLBM_ERR_UNSUPPORTED for other storage formats.
+ * tlbm_bounds_check_word waits for the engine's stream,
  * returns the word (0: no violation) and clears it.
  */
 tlbm_status tlbm_set_bounds_check(tlbm *t, int on);
@@ -385,17 +387,18 @@ tlbm_status tlbm_bounds_check_word(tlbm *t, uint64_t *word);
  *       enters through the source of Guo, Zheng and Shi (2002) at the fluid
  *       velocity u = (j + F/2)/rho.  In the continuum F = -(rho grad mu_rho +
  *       phi grad mu_phi + psi grad mu_psi); on the lattice sum_r F = 0 exactly.
- *       g and k are unchanged.  Three kernels per step (moments; Pi_ab, mu_phi,
- *       mu_psi arrays; collide+stream); no fused kernel.
+ *       g and k are unchanged.  TLBM_KERNEL_FUSED (the AUTO choice) runs one
+ *       marching kernel per step (moments with a two-node halo and a ring of
+ *       Pi planes in shared memory); TLBM_KERNEL_SPLIT three kernels
+ *       (moments; Pi_ab, mu_phi, mu_psi node arrays; collide+stream).
  */
 typedef enum { TLBM_COUPLING_PRESSURE_TENSOR = 0, TLBM_COUPLING_FORCING = 1 } tlbm_coupling;
 
 /*
  * Select the coupling.  TLBM_COUPLING_FORCING needs a lattice without solid
- * nodes and an engine whose kernel choice is not TLBM_KERNEL_FUSED
- * (TLBM_ERR_UNSUPPORTED otherwise); it allocates (NPI + 2) node arrays of the
- * compute type, NPI = 3 on D2Q9 and 6 on D3Q19 (TLBM_ERR_OOM if that fails),
- * which tlbm_destroy frees.  The populations are left as they are: call
+ * nodes (TLBM_ERR_UNSUPPORTED otherwise); it allocates (NPI + 2) node arrays
+ * of the compute type for the split kernels, NPI = 3 on D2Q9 and 6 on D3Q19
+ * (TLBM_ERR_OOM if that fails), which tlbm_destroy frees.  The populations are left as they are: call
  * tlbm_init_fields afterwards to start from the coupling's own equilibrium
  * (under forcing, the u given there is the stored momentum over rho; the
  * fluid velocity adds F/(2 rho)).  Under forcing, tlbm_fields returns the

@@ -337,9 +337,6 @@ tlbm_status tlbm_set_coupling(tlbm* t, tlbm_coupling coupling) {
     if (coupling == TLBM_COUPLING_FORCING) {
         if (t->d.solid)
             return fail(t, TLBM_ERR_UNSUPPORTED, "the forcing coupling runs on lattices without solid nodes");
-        if (t->kind_req == TLBM_KERNEL_FUSED)
-            return fail(t, TLBM_ERR_UNSUPPORTED,
-                        "the fused kernels carry the pressure-tensor coupling only; select TLBM_KERNEL_AUTO or SPLIT");
         tlbm_status s = ensure_mom(t);
         if (s != TLBM_OK) return s;
         if (!t->d.aux)

@@ -960,7 +960,11 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
     const int variant = dbl ? 0 : (tile & 15);
     int mc = tile >> 8;
     FusedCfg<Q> c{};
-    if (d.solid) {
+    if (d.coupling) {
+        // forcing coupling (k_guo_fused): the solid-aware kernel's tiles (two-node halo)
+        c.TX = Q == 19 ? (dbl ? 16 : 32) : 128;
+        c.TY = Q == 19 ? 4 : 1;
+    } else if (d.solid) {
         // solid-aware kernel: a fixed tile per lattice (D3Q19 in double: 16x4 keeps
         // its five-plane rings under the 48 KB static shared-memory limit)
         c.TX = Q == 19 ? (dbl ? 16 : 32) : (dbl ? 128 : (variant == 2 ? 256 : (variant == 3 ? 64 : 128)));

@@ -60,9 +60,11 @@ struct Impl {
     static int aux_per_node() { return GuoAux<Q>::NA; }
 
     static cudaError_t step(DevState& d, int kind, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1) {
-        if (d.coupling) kind = tlbm_host::KIND_SPLIT;  // the fused kernels carry the pressure tensor only
         if (ev0) cudaEventRecord(ev0, st);
-        if (d.coupling) {
+        if (d.coupling && kind == tlbm_host::KIND_FUSED) {
+            cudaError_t e = guo_fused_step<Q, S>(d, to_phys<T>(d.phys), st);
+            if (e != cudaSuccess) return e;
+        } else if (d.coupling) {
             guo(d, st);
         } else if (kind == tlbm_host::KIND_FUSED) {
             cudaError_t e = fused_step<Q, S>(d, to_phys<T>(d.phys), st);
@@ -149,12 +151,12 @@ struct Impl {
     }
 
     static int launches(const DevState& d, int kind) {
-        if (d.coupling) return 3 + 1;
         if (kind == tlbm_host::KIND_FUSED) return fused_launches<Q, S>(d) + 1;
+        if (d.coupling) return 3 + 1;
         return (d.solid ? 3 : 2) + 1;
     }
 
-    static bool has_fused(const DevState& d) { return !d.coupling && fused_supported<Q, S>(d); }
+    static bool has_fused(const DevState& d) { return fused_supported<Q, S>(d); }
 
     template <bool SOLID>
     static cudaError_t adjoint_run(DevState& d, int kind, const tlbm_host::AdjJob& J, cudaStream_t st) {
