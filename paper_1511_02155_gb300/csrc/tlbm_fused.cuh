@@ -275,8 +275,9 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const unsigned char* p0 = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
-            const T f = ldp(p0, 0, i);
-            const T gg = ldp(p0, 1, i);
+            T f, gg;
+            if (Fmt<Q, S>::PACKED && i > 0) Fmt<Q, S>::ld_fg(p0, i, f, gg);  // one lane word
+            else f = ldp(p0, 0, i), gg = ldp(p0, 1, i);
             const T kk = ldp(p0, 2, i);
             rho0 += f;
             if (A::ca(i)) ja += T(A::ca(i)) * f;
@@ -294,8 +295,15 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
             }
             if (ILP && two) {  // border node of this thread, loads interleaved with node 0
                 const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                rho1 += ldp(p1, 0, i);
-                phi1 += ldp(p1, 1, i);
+                if (Fmt<Q, S>::PACKED && i > 0) {
+                    T a, b;
+                    Fmt<Q, S>::ld_fg(p1, i, a, b);
+                    rho1 += a;
+                    phi1 += b;
+                } else {
+                    rho1 += ldp(p1, 0, i);
+                    phi1 += ldp(p1, 1, i);
+                }
                 psi1 += ldp(p1, 2, i);
             }
         }
@@ -303,8 +311,15 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                rho1 += ldp(p1, 0, i);
-                phi1 += ldp(p1, 1, i);
+                if (Fmt<Q, S>::PACKED && i > 0) {
+                    T a, b;
+                    Fmt<Q, S>::ld_fg(p1, i, a, b);
+                    rho1 += a;
+                    phi1 += b;
+                } else {
+                    rho1 += ldp(p1, 0, i);
+                    phi1 += ldp(p1, 1, i);
+                }
                 psi1 += ldp(p1, 2, i);
             }
         }
@@ -353,12 +368,20 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
                     const T* sp = stg + (size_t)((m & 1) * STG) * NT + tid;
                     const int r0 = stage_rank<Q, STGO>(0, i), r1 = stage_rank<Q, STGO>(1, i),
                               r2 = stage_rank<Q, STGO>(2, i);
-                    fv[i] = r0 < STG ? sp[(size_t)r0 * NT] : lc(0);
-                    gv[i] = r1 < STG ? sp[(size_t)r1 * NT] : lc(1);
+                    if (Fmt<Q, S>::PACKED && i > 0 && r0 >= STG && r1 >= STG) {
+                        Fmt<Q, S>::template ld_fg<(HINT >= 2)>(pi, i, fv[i], gv[i]);  // one lane word
+                    } else {
+                        fv[i] = r0 < STG ? sp[(size_t)r0 * NT] : lc(0);
+                        gv[i] = r1 < STG ? sp[(size_t)r1 * NT] : lc(1);
+                    }
                     kv[i] = r2 < STG ? sp[(size_t)r2 * NT] : lc(2);
                 } else {
-                    fv[i] = lc(0);
-                    gv[i] = lc(1);
+                    if (Fmt<Q, S>::PACKED && i > 0) {
+                        Fmt<Q, S>::template ld_fg<(HINT >= 2)>(pi, i, fv[i], gv[i]);
+                    } else {
+                        fv[i] = lc(0);
+                        gv[i] = lc(1);
+                    }
                     kv[i] = lc(2);
                 }
             }
@@ -460,12 +483,18 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
                 const T v[6] = {cf * fv[i] + (evf + odf), cf * fv[o] + (evf - odf),
                                 cg * gv[i] + (evg + odg), cg * gv[o] + (evg - odg),
                                 ck * kv[i] + (evk + odk), ck * kv[o] + (evk - odk)};
-                st_(out, 0, i, v[0]);
-                st_(out, 0, o, v[1]);
-                st_(out, 1, i, v[2]);
-                st_(out, 1, o, v[3]);
-                st_(out, 2, i, v[4]);
-                st_(out, 2, o, v[5]);
+                if constexpr (Fmt<Q, S>::PACKED) {  // three 32-bit lane words
+                    Fmt<Q, S>::template st_fg<(HINT >= 1)>(out, i, v[0], v[2]);
+                    Fmt<Q, S>::template st_fg<(HINT >= 1)>(out, o, v[1], v[3]);
+                    Fmt<Q, S>::template st_kk<(HINT >= 1)>(out, i, v[4], v[5]);
+                } else {
+                    st_(out, 0, i, v[0]);
+                    st_(out, 0, o, v[1]);
+                    st_(out, 1, i, v[2]);
+                    st_(out, 1, o, v[3]);
+                    st_(out, 2, i, v[4]);
+                    st_(out, 2, o, v[5]);
+                }
                 if (OF) {
                     qf += Fmt<Q, S>::qdelta_d(i, v[0]) + Fmt<Q, S>::qdelta_d(o, v[1]);
                     qg += Fmt<Q, S>::qdelta_d(i, v[2]) + Fmt<Q, S>::qdelta_d(o, v[3]);
@@ -637,16 +666,21 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
                 for (int i = 0; i < Q; ++i) {
                     // pull source, or this node's opposite run when the source is solid:
                     // one pointer select, then loads at the run offsets of direction i
+                    // (pointer selects per set: f and g of a direction move together, k apart)
                     const unsigned char* p =
                         chk_node<Q, S, CHK>(g, srcb, row_ptr(k, zr, A::cb(i), A::cm(i)) + xc[k][1 - A::ca(i)], 1);
-                    if (i > 0 && ((mk >> i) & 1u)) p = own + Fmt<Q, S>::run_gap(i, opp<Q>(i));
-                    const T f = Fmt<Q, S>::ld_delta(p, 0, i);
+                    const bool bb = i > 0 && ((mk >> i) & 1u);
+                    const unsigned char* pfg = bb ? own + (Fmt<Q, S>::off(0, opp<Q>(i)) - Fmt<Q, S>::off(0, i)) : p;
+                    const unsigned char* pk = bb ? own + (Fmt<Q, S>::off(2, opp<Q>(i)) - Fmt<Q, S>::off(2, i)) : p;
+                    T f, gv;
+                    if (i > 0) Fmt<Q, S>::ld_fg(pfg, i, f, gv);
+                    else f = Fmt<Q, S>::ld_delta(p, 0, 0), gv = Fmt<Q, S>::ld_delta(p, 1, 0);
                     rd += f;
                     if (A::ca(i)) ja += T(A::ca(i)) * f;
                     if (A::cb(i)) jb += T(A::cb(i)) * f;
                     if (A::cm(i)) jm += T(A::cm(i)) * f;
-                    phi += Fmt<Q, S>::ld_delta(p, 1, i);
-                    psi += Fmt<Q, S>::ld_delta(p, 2, i);
+                    phi += gv;
+                    psi += Fmt<Q, S>::ld_delta(pk, 2, i);
                 }
             }
             const T rho = (mk & 1u) ? T(0) : (Fmt<Q, S>::OFFSET ? T(1) + rd : rd);
@@ -779,10 +813,19 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const unsigned char* p = chk_node<Q, S, CHK>(g, srcb, own_row(zr, A::cb(i), A::cm(i)) + xo[1 - A::ca(i)], 1);
-            if (i > 0 && ((mk >> i) & 1u)) p = own + Fmt<Q, S>::run_gap(i, opp<Q>(i));
-            fv[i] = Fmt<Q, S>::ld(p, 0, i);
-            gv[i] = Fmt<Q, S>::ld(p, 1, i);
-            kv[i] = Fmt<Q, S>::ld(p, 2, i);
+            const bool bb = i > 0 && ((mk >> i) & 1u);
+            const unsigned char* pfg = bb ? own + (Fmt<Q, S>::off(0, opp<Q>(i)) - Fmt<Q, S>::off(0, i)) : p;
+            const unsigned char* pk = bb ? own + (Fmt<Q, S>::off(2, opp<Q>(i)) - Fmt<Q, S>::off(2, i)) : p;
+            if (i > 0) {
+                T df, dg;
+                Fmt<Q, S>::ld_fg(pfg, i, df, dg);
+                fv[i] = Fmt<Q, S>::unbias(0, i, df);
+                gv[i] = dg;
+            } else {
+                fv[i] = Fmt<Q, S>::ld(p, 0, 0);
+                gv[i] = Fmt<Q, S>::ld(p, 1, 0);
+            }
+            kv[i] = Fmt<Q, S>::ld(pk, 2, i);
         }
 
         // ---- collide + store (same arithmetic as k_fused)
@@ -812,12 +855,9 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
             const T v[6] = {cf * fv[i] + (evf + odf), cf * fv[o] + (evf - odf),
                             cg * gv[i] + (evg + odg), cg * gv[o] + (evg - odg),
                             ck * kv[i] + (evk + odk), ck * kv[o] + (evk - odk)};
-            Fmt<Q, S>::st(out, 0, i, v[0]);
-            Fmt<Q, S>::st(out, 0, o, v[1]);
-            Fmt<Q, S>::st(out, 1, i, v[2]);
-            Fmt<Q, S>::st(out, 1, o, v[3]);
-            Fmt<Q, S>::st(out, 2, i, v[4]);
-            Fmt<Q, S>::st(out, 2, o, v[5]);
+            Fmt<Q, S>::template st_fg<false>(out, i, Fmt<Q, S>::dev(0, i, v[0]), v[2]);
+            Fmt<Q, S>::template st_fg<false>(out, o, Fmt<Q, S>::dev(0, o, v[1]), v[3]);
+            Fmt<Q, S>::template st_kk<false>(out, i, v[4], v[5]);
             if (Fmt<Q, S>::OFFSET) {
                 qf += Fmt<Q, S>::qdelta(0, i, v[0]) + Fmt<Q, S>::qdelta(0, o, v[1]);
                 qg += Fmt<Q, S>::qdelta(1, i, v[2]) + Fmt<Q, S>::qdelta(1, o, v[3]);

@@ -133,6 +133,16 @@ struct Store<__half> {
     using T = float;
     static __device__ __forceinline__ float get(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half put(float v) { return __float2half_rn(v); }
+    // a 32-bit lane word of two values (low half first)
+    static __device__ __forceinline__ void get2(unsigned w, float& a, float& b) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ unsigned put2(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const unsigned*>(&h);
+    }
 };
 
 template <>
@@ -140,6 +150,16 @@ struct Store<__nv_bfloat16> {
     using T = float;
     static __device__ __forceinline__ float get(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 put(float v) { return __float2bfloat16_rn(v); }
+    // a 32-bit lane word of two values (low half first)
+    static __device__ __forceinline__ void get2(unsigned w, float& a, float& b) {
+        const float2 v = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ unsigned put2(float a, float b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const unsigned*>(&h);
+    }
 };
 
 // ------------------------------------------------------------------ geometry
@@ -147,22 +167,27 @@ struct Store<__nv_bfloat16> {
 // Population layout: 32-node chunks along x.  All populations of the 32 nodes
 // x = 32c .. 32c+31 of one row (row = y + ny*z) form one contiguous chunk of
 // Fmt<Q,S>::CHUNK bytes at ((row * ncx + c) * CHUNK), ncx = ceil(nx / 32).
-// Inside a chunk, each run holds one value per lane (node), sizeof(S) bytes
-// apart, so a node is one byte offset: chunk + lane * sizeof(S).
+// Inside a chunk, each run holds one lane word per node, Fmt::ESZ bytes apart,
+// so a node is one byte offset, chunk + lane * ESZ, and every population of it
+// is that offset plus a constant.
 //   FP64 / FP32: 3Q runs of S, run s*Q + i for set s, direction i.  FP32 keeps
 //     f as its deviation f_i - w_i from the rest state at rho = 1 (g and k as
 //     they are): deviations are small, so FP32 rounding of the stored values,
 //     and with it the drift of the total momentum, is ~100x smaller.
 //   16-bit formats (packed): f is kept as its deviation f_i - w_i from the
-//     rest state at rho = 1, g and k as they are.  The 3(Q-1) moving directions
-//     i >= 1 are 16-bit runs; the rest populations f_0 - w_0, g_0, k_0 are FP32,
-//     each split into a run of low and a run of high 16-bit halves.  The rest
-//     populations carry nearly all of phi and psi, which 16 bits would round by
-//     up to 2.4e-4 per step; the moving populations are small.  A collision
-//     writes each rest population as the node's moment minus the moving
-//     populations as stored (rounded), so the 16-bit rounding moves mass
-//     between directions of a node but never changes it; rho - 1 is summed from
-//     the small deviations, which keeps FP32 rounding from biasing the totals.
+//     rest state at rho = 1, g and k as they are.  Every lane word is 32 bits:
+//     for each moving direction i one run of (f_i, g_i) pairs (the two share a
+//     pull source: one load), for each pair of opposite directions i < opp(i)
+//     one run of (k_i, k_opp(i)) pairs (the collision writes both at once: one
+//     store), and three FP32 runs of the rest populations f_0 - w_0, g_0, k_0.
+//     That is 3(Q-1) 16-bit values and three FP32 values per node, as dense as
+//     16 bits allow.  The rest populations carry nearly all of phi and psi,
+//     which 16 bits would round by up to 2.4e-4 per step; the moving
+//     populations are small.  A collision writes each rest population as the
+//     node's moment minus the moving populations as stored (rounded), so the
+//     16-bit rounding moves mass between directions of a node but never changes
+//     it; rho - 1 is summed from the small deviations, which keeps FP32
+//     rounding from biasing the totals.
 // A warp on 32 consecutive x of one row therefore finds all populations of its
 // nodes in one chunk: each load or store is one base address plus an immediate
 // offset.  Padding nodes (x >= nx in the last chunk) are never read or written.
@@ -180,35 +205,59 @@ struct Fmt {
     // f kept as its deviation f_i - w_i from the rest state at rho = 1 (FP32 and
     // the 16-bit formats; FP64 stores f as it is)
     static constexpr bool OFFSET = sizeof(S) <= 4;
-    static constexpr int ESZ = (int)sizeof(S);  // bytes between lanes of a run
-    static constexpr long long CHUNK = PACKED ? (3LL * Q + 3) * 32 * 2 : 3LL * Q * 32 * ESZ;
-    // byte offset of lane 0 of the run of (s, i) (packed rest: its low halves)
-    __host__ __device__ static constexpr int off(int s, int i) {
-        return PACKED ? (i == 0 ? (3 * (Q - 1) + 2 * s) * 32 * 2 : (s * (Q - 1) + i - 1) * 32 * 2)
-                      : (s * Q + i) * 32 * ESZ;
+    static constexpr int ESZ = PACKED ? 4 : (int)sizeof(S);  // bytes between lanes of a run
+    static constexpr int NKP = (Q - 1) / 2;                  // runs of k pairs (packed)
+    static constexpr long long CHUNK = PACKED ? ((Q - 1) + NKP + 3) * 128LL : 3LL * Q * 32 * ESZ;
+    // packed: run of the k pair of direction i (the pairs of opposite directions
+    // numbered by their lower direction), and the half of its lane word (0: i is
+    // the lower direction of its pair).  Tables, so that they fold to immediates.
+    __host__ __device__ static constexpr int kpair(int i) {
+        if (Q == 19) {
+            // pairs (1,2) (3,4) (5,6) (7,10) (8,9) (11,14) (12,13) (15,18) (16,17)
+            constexpr int v[19] = {0, 0, 0, 1, 1, 2, 2, 3, 4, 4, 3, 5, 6, 6, 5, 7, 8, 8, 7};
+            return v[i];
+        }
+        // D2Q9: opposites adjacent, pairs (1,2) (3,4) (5,6) (7,8)
+        return (i - 1) / 2;
     }
-    // byte distance from the run of (s, i) to the run of (s, j) -- the same for
-    // every set s when i, j >= 1
-    __host__ __device__ static constexpr int run_gap(int i, int j) { return off(0, j) - off(0, i); }
-    // rest-state value subtracted before storage (packed formats, set f)
+    __host__ __device__ static constexpr int khalf(int i) {
+        if (Q == 19) {
+            constexpr int v[19] = {0, 0, 1, 0, 1, 0, 1, 0, 0, 1, 1, 0, 0, 1, 1, 0, 0, 1, 1};
+            return v[i];
+        }
+        return (i - 1) & 1;
+    }
+    // byte offset of (s, i) in the lane word of lane 0
+    __host__ __device__ static constexpr int off(int s, int i) {
+        if (!PACKED) return (s * Q + i) * 32 * ESZ;
+        if (i == 0) return ((Q - 1) + NKP + s) * 128;
+        if (s < 2) return (i - 1) * 128 + 2 * s;
+        return ((Q - 1) + kpair(i)) * 128 + 2 * khalf(i);
+    }
+    // rest-state value subtracted before storage (set f, offset formats)
     __host__ __device__ static constexpr double bias(int s, int i) {
         return (OFFSET && s == 0) ? Lat<Q>::w(i) : 0.0;
     }
     // stored value of (s, i) at node pointer n (chunk + lane * ESZ): x - bias
     static __device__ __forceinline__ T ld_delta(const unsigned char* n, int s, int i) {
         if constexpr (PACKED) {
-            if (i == 0) {
-                const unsigned lo = *reinterpret_cast<const unsigned short*>(n + off(s, 0));
-                const unsigned hi = *reinterpret_cast<const unsigned short*>(n + off(s, 0) + 64);
-                return __uint_as_float(lo | (hi << 16));
-            }
+            if (i == 0) return *reinterpret_cast<const float*>(n + off(s, 0));
             return Store<S>::get(*reinterpret_cast<const S*>(n + off(s, i)));
         } else {
             return *reinterpret_cast<const S*>(n + off(s, i));
         }
     }
-    // population (s, i) at node pointer n (no add where the bias is zero: x + 0
-    // is not x for x = -0, so the compiler would keep it)
+    // value from its stored deviation and back (no add where the bias is zero:
+    // x + 0 is not x for x = -0, so the compiler would keep it)
+    static __device__ __forceinline__ T unbias(int s, int i, T d) {
+        const double b = bias(s, i);
+        return b == 0.0 ? d : d + T(b);
+    }
+    static __device__ __forceinline__ T dev(int s, int i, T v) {
+        const double b = bias(s, i);
+        return b == 0.0 ? v : v - T(b);
+    }
+    // population (s, i) at node pointer n
     static __device__ __forceinline__ T ld(const unsigned char* n, int s, int i) {
         const double b = bias(s, i);
         return b == 0.0 ? ld_delta(n, s, i) : ld_delta(n, s, i) + T(b);
@@ -221,26 +270,29 @@ struct Fmt {
     // stored value of (s, i), marking the line evict-first (its last use)
     static __device__ __forceinline__ T ld_last_delta(const unsigned char* n, int s, int i) {
         if constexpr (PACKED) {
-            if (i == 0) {
-                const unsigned lo = __ldcs(reinterpret_cast<const unsigned short*>(n + off(s, 0)));
-                const unsigned hi = __ldcs(reinterpret_cast<const unsigned short*>(n + off(s, 0) + 64));
-                return __uint_as_float(lo | (hi << 16));
-            }
+            if (i == 0) return __ldcs(reinterpret_cast<const float*>(n + off(s, 0)));
             return Store<S>::get(__ldcs(reinterpret_cast<const S*>(n + off(s, i))));
         } else {
             return __ldcs(reinterpret_cast<const S*>(n + off(s, i)));
         }
     }
+    // stored values of f_i and g_i, i >= 1, at node pointer n (packed: one load
+    // of their lane word; LAST marks it evict-first)
+    template <bool LAST = false>
+    static __device__ __forceinline__ void ld_fg(const unsigned char* n, int i, T& f, T& g) {
+        if constexpr (PACKED) {
+            const unsigned* p = reinterpret_cast<const unsigned*>(n + off(0, i));
+            Store<S>::get2(LAST ? __ldcs(p) : *p, f, g);
+        } else {
+            f = LAST ? ld_last_delta(n, 0, i) : ld_delta(n, 0, i);
+            g = LAST ? ld_last_delta(n, 1, i) : ld_delta(n, 1, i);
+        }
+    }
     // store the deviation d of (s, i) with an evict-first hint
     static __device__ __forceinline__ void st_stream_delta(unsigned char* n, int s, int i, T d) {
         if constexpr (PACKED) {
-            if (i == 0) {
-                const unsigned u = __float_as_uint(d);
-                __stcs(reinterpret_cast<unsigned short*>(n + off(s, 0)), (unsigned short)(u & 0xffffu));
-                __stcs(reinterpret_cast<unsigned short*>(n + off(s, 0) + 64), (unsigned short)(u >> 16));
-            } else {
-                __stcs(reinterpret_cast<S*>(n + off(s, i)), Store<S>::put(d));
-            }
+            if (i == 0) __stcs(reinterpret_cast<float*>(n + off(s, 0)), d);
+            else __stcs(reinterpret_cast<S*>(n + off(s, i)), Store<S>::put(d));
         } else {
             __stcs(reinterpret_cast<S*>(n + off(s, i)), d);
         }
@@ -254,30 +306,14 @@ struct Fmt {
     }
     // store with an evict-first hint (streamed out, read only by the next step)
     static __device__ __forceinline__ void st_stream(unsigned char* n, int s, int i, T v) {
-        if constexpr (PACKED) {
-            const double b = bias(s, i);
-            const T d = b == 0.0 ? v : v - T(b);
-            if (i == 0) {
-                const unsigned u = __float_as_uint(d);
-                __stcs(reinterpret_cast<unsigned short*>(n + off(s, 0)), (unsigned short)(u & 0xffffu));
-                __stcs(reinterpret_cast<unsigned short*>(n + off(s, 0) + 64), (unsigned short)(u >> 16));
-            } else {
-                __stcs(reinterpret_cast<S*>(n + off(s, i)), Store<S>::put(d));
-            }
-        } else {
-            __stcs(reinterpret_cast<S*>(n + off(s, i)), v);
-        }
+        const double b = bias(s, i);
+        st_stream_delta(n, s, i, b == 0.0 ? v : v - T(b));
     }
     // store the deviation d = x - bias of (s, i)
     static __device__ __forceinline__ void st_delta(unsigned char* n, int s, int i, T d) {
         if constexpr (PACKED) {
-            if (i == 0) {
-                const unsigned u = __float_as_uint(d);
-                *reinterpret_cast<unsigned short*>(n + off(s, 0)) = (unsigned short)(u & 0xffffu);
-                *reinterpret_cast<unsigned short*>(n + off(s, 0) + 64) = (unsigned short)(u >> 16);
-            } else {
-                *reinterpret_cast<S*>(n + off(s, i)) = Store<S>::put(d);
-            }
+            if (i == 0) *reinterpret_cast<float*>(n + off(s, 0)) = d;
+            else *reinterpret_cast<S*>(n + off(s, i)) = Store<S>::put(d);
         } else {
             *reinterpret_cast<S*>(n + off(s, i)) = d;
         }
@@ -285,6 +321,39 @@ struct Fmt {
     static __device__ __forceinline__ void st(unsigned char* n, int s, int i, T v) {
         const double b = bias(s, i);
         st_delta(n, s, i, b == 0.0 ? v : v - T(b));
+    }
+    // store the deviations of f_i, g_i (i >= 1) and, in a second call, of k_i and
+    // k_o for o = opp(i) (packed: one 32-bit store each; STREAM: evict-first)
+    template <bool STREAM>
+    static __device__ __forceinline__ void st_fg(unsigned char* n, int i, T df, T dg) {
+        if constexpr (PACKED) {
+            unsigned* p = reinterpret_cast<unsigned*>(n + off(0, i));
+            const unsigned w = Store<S>::put2(df, dg);
+            if (STREAM) __stcs(p, w);
+            else *p = w;
+        } else if (STREAM) {
+            st_stream_delta(n, 0, i, df);
+            st_stream_delta(n, 1, i, dg);
+        } else {
+            st_delta(n, 0, i, df);
+            st_delta(n, 1, i, dg);
+        }
+    }
+    template <bool STREAM>
+    static __device__ __forceinline__ void st_kk(unsigned char* n, int i, T dki, T dko) {
+        if constexpr (PACKED) {
+            const bool lo = khalf(i) == 0;  // the lower direction sits in the low half
+            unsigned* p = reinterpret_cast<unsigned*>(n + off(2, lo ? i : opp<Q>(i)));
+            const unsigned w = lo ? Store<S>::put2(dki, dko) : Store<S>::put2(dko, dki);
+            if (STREAM) __stcs(p, w);
+            else *p = w;
+        } else if (STREAM) {
+            st_stream_delta(n, 2, i, dki);
+            st_stream_delta(n, 2, opp<Q>(i), dko);
+        } else {
+            st_delta(n, 2, i, dki);
+            st_delta(n, 2, opp<Q>(i), dko);
+        }
     }
     // the deviation a store of population value v leaves in memory, as read back
     static __device__ __forceinline__ T qdelta(int s, int i, T v) {
