@@ -122,11 +122,12 @@ tlbm_status tlbm_set_kernel(tlbm *t, tlbm_kernel kind);
 tlbm_kernel tlbm_get_kernel(const tlbm *t);
 
 /* Tile of the fused step.  variant = shape | mode << 4: shape 0 = default
- * (shape 5 on both lattices), D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4 nodes
- * per block, 4..6 = 32x4 with part of each node's pulled populations kept in
+ * (D3Q19 shape 7, D2Q9 shape 5), D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4 nodes
+ * per block, 4..7 = 32x4 with part of each node's pulled populations kept in
  * shared memory from the moment pass to the collision (4: the 19 f values;
  * 5: the lane-shifted values first, 28 for FP32, 19 plus a per-warp L2
- * prefetch for the 16-bit formats; 6: 19 lane-shifted values); D2Q9 1 = 128,
+ * prefetch for the 16-bit formats; 6: 19 lane-shifted values; 7: as 5, the
+ * k values first and then the lane-shifted (f, g) pairs); D2Q9 1 = 128,
  * 2 = 256, 3 = 64 nodes per row, 4 = 128 with the 18 lane-shifted values
  * staged, 5 = 128 with all 27 staged.  mode (shapes 1..3) selects the
  * load order and cache hints inside a plane (0 default for the lattice and
@@ -134,7 +135,7 @@ tlbm_kernel tlbm_get_kernel(const tlbm *t);
  * 4 per-warp L2 prefetch three planes ahead; 5 = 1 + 4; 6 plain order;
  * 8 evict-first stores; 9 also evict-first collision loads; 12, 13 = 8, 9 with
  * the prefetch; a mode not built for a shape falls back to its default; the
- * variant must be below 256, its shape below 7).
+ * variant must be below 256, its shape below 8).
  * chunk = planes marched per block (0 = chosen from the lattice size).  Double
  * storage ignores the choice.  Results do not depend on the tile. */
 tlbm_status tlbm_set_tile(tlbm *t, int variant, int chunk);

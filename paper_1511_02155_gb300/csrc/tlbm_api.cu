@@ -233,10 +233,14 @@ tlbm_status tlbm_create(tlbm** out, tlbm_lattice lattice, int nx, int ny, int nz
     d.nx = nx; d.ny = ny; d.nz = nz; d.N = N;
     d.Np = (N + 63) / 64 * 64;
     d.ncx = (nx + 31) / 32;
-    // bytes of one 32-node chunk (see the layout notes in tlbm_lattice.cuh): all
-    // 3Q populations of the storage type, or for the 16-bit formats 3(Q-1)
-    // 16-bit moving populations plus three FP32 rest populations
-    const long long chunk = esize == 2 ? (3LL * (d.Q - 1) * 32 * 2 + 3LL * 32 * 4) : 3LL * d.Q * 32 * (long long)esize;
+    // bytes of one 32-node chunk (see the layout notes in tlbm_lattice.cuh): FP64
+    // and D2Q9 FP32 all 3Q populations; D3Q19 FP32 3(Q-1)/2 runs of two-value
+    // lane words for the moving populations and two for the rest populations
+    // (one value unused); 16-bit formats 3(Q-1)/2 runs of 16-bit pairs and three
+    // FP32 rest runs
+    const long long chunk = esize == 2   ? (long long)((d.Q - 1) + (d.Q - 1) / 2 + 3) * 128
+                            : esize == 4 && d.Q == 19 ? (long long)((d.Q - 1) + (d.Q - 1) / 2 + 2) * 256
+                                         : 3LL * d.Q * 32 * (long long)esize;
     d.pop_bytes = (long long)ny * nz * d.ncx * chunk;
     d.cur = 0;
     d.tile = 0;
@@ -323,7 +327,7 @@ tlbm_kernel tlbm_get_kernel(const tlbm* t) {
 // Tile choice of the fused step: variant (0 = default) and planes per chunk (0 = auto).
 tlbm_status tlbm_set_tile(tlbm* t, int variant, int chunk) {
     if (!t) return TLBM_ERR_ARG;
-    if (variant < 0 || variant > 255 || (variant & 15) > 6 || chunk < 0 || chunk > 4096)
+    if (variant < 0 || variant > 255 || (variant & 15) > 7 || chunk < 0 || chunk > 4096)
         return fail(t, TLBM_ERR_ARG, "bad tile");
     t->d.tile = variant + 256 * chunk;
     // partial sums must fit: blocks grow as chunks shrink
@@ -772,7 +776,7 @@ int64_t tlbm_batch_blocks(const tlbm_batch* b) { return b ? (int64_t)b->bs.block
 
 tlbm_status tlbm_batch_set_tile(tlbm_batch* b, int variant, int chunk) {
     if (!b) return TLBM_ERR_ARG;
-    if (variant < 0 || variant > 255 || (variant & 15) > 6 || chunk < 0 || chunk > 4096)
+    if (variant < 0 || variant > 255 || (variant & 15) > 7 || chunk < 0 || chunk > 4096)
         return bfail(b, TLBM_ERR_ARG, "bad tile");
     const int old = b->bs.tile;
     b->bs.tile = variant + 256 * chunk;

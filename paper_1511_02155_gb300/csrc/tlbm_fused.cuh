@@ -114,6 +114,14 @@ __host__ __device__ constexpr int stage_rank(int s, int i) {
         const bool sh = (i == 1 || i == 2) || (i >= 7 && i <= 10) || (i >= 15);
         const int is = i <= 2 ? i - 1 : (i <= 10 ? i - 5 : i - 9);
         const int iu = i == 0 ? 0 : (i <= 6 ? i - 2 : i - 6);
+        if (STGO == 2) {
+            // paired lane words: the k values first (each a lone value of its
+            // word), lane-shifted first; then the lane-shifted (f, g) pairs; then
+            // the other pairs and the rest populations
+            if (i == 0) return 54 + s;
+            if (s == 2) return sh ? is : 10 + iu - 1;
+            return 18 + (sh ? 2 * is + s : 20 + 2 * (iu - 1) + s);
+        }
         return sh ? s * 10 + is : 30 + s * 9 + iu;
     }
     const bool sh = i == 1 || i == 2 || i >= 5;
@@ -276,7 +284,7 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
         for (int i = 0; i < Q; ++i) {
             const unsigned char* p0 = src_of(0, zr, A::ca(i), A::cb(i), A::cm(i));
             T f, gg;
-            if (Fmt<Q, S>::PACKED && i > 0) Fmt<Q, S>::ld_fg(p0, i, f, gg);  // one lane word
+            if (Fmt<Q, S>::PAIRED && i > 0) Fmt<Q, S>::ld_fg(p0, i, f, gg);  // one lane word
             else f = ldp(p0, 0, i), gg = ldp(p0, 1, i);
             const T kk = ldp(p0, 2, i);
             rho0 += f;
@@ -295,7 +303,7 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
             }
             if (ILP && two) {  // border node of this thread, loads interleaved with node 0
                 const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                if (Fmt<Q, S>::PACKED && i > 0) {
+                if (Fmt<Q, S>::PAIRED && i > 0) {
                     T a, b;
                     Fmt<Q, S>::ld_fg(p1, i, a, b);
                     rho1 += a;
@@ -311,7 +319,7 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const unsigned char* p1 = src_of(1, zr, A::ca(i), A::cb(i), A::cm(i));
-                if (Fmt<Q, S>::PACKED && i > 0) {
+                if (Fmt<Q, S>::PAIRED && i > 0) {
                     T a, b;
                     Fmt<Q, S>::ld_fg(p1, i, a, b);
                     rho1 += a;
@@ -368,7 +376,7 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
                     const T* sp = stg + (size_t)((m & 1) * STG) * NT + tid;
                     const int r0 = stage_rank<Q, STGO>(0, i), r1 = stage_rank<Q, STGO>(1, i),
                               r2 = stage_rank<Q, STGO>(2, i);
-                    if (Fmt<Q, S>::PACKED && i > 0 && r0 >= STG && r1 >= STG) {
+                    if (Fmt<Q, S>::PAIRED && i > 0 && r0 >= STG && r1 >= STG) {
                         Fmt<Q, S>::template ld_fg<(HINT >= 2)>(pi, i, fv[i], gv[i]);  // one lane word
                     } else {
                         fv[i] = r0 < STG ? sp[(size_t)r0 * NT] : lc(0);
@@ -376,7 +384,7 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
                     }
                     kv[i] = r2 < STG ? sp[(size_t)r2 * NT] : lc(2);
                 } else {
-                    if (Fmt<Q, S>::PACKED && i > 0) {
+                    if (Fmt<Q, S>::PAIRED && i > 0) {
                         Fmt<Q, S>::template ld_fg<(HINT >= 2)>(pi, i, fv[i], gv[i]);
                     } else {
                         fv[i] = lc(0);
@@ -483,7 +491,7 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
                 const T v[6] = {cf * fv[i] + (evf + odf), cf * fv[o] + (evf - odf),
                                 cg * gv[i] + (evg + odg), cg * gv[o] + (evg - odg),
                                 ck * kv[i] + (evk + odk), ck * kv[o] + (evk - odk)};
-                if constexpr (Fmt<Q, S>::PACKED) {  // three 32-bit lane words
+                if constexpr (Fmt<Q, S>::PAIRED) {  // three lane words
                     Fmt<Q, S>::template st_fg<(HINT >= 1)>(out, i, v[0], v[2]);
                     Fmt<Q, S>::template st_fg<(HINT >= 1)>(out, o, v[1], v[3]);
                     Fmt<Q, S>::template st_kk<(HINT >= 1)>(out, i, v[4], v[5]);
@@ -978,14 +986,16 @@ template <int Q>
 struct FusedCfg {
     int TX, TY, MC;
     int mode;
-    int shape;  // resolved D3Q19 shape (4..6: 32x4 kernels with staging)
+    int shape;  // resolved D3Q19 shape (4..7: 32x4 kernels with staging)
 };
 
-// d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 shape 5,
-// D2Q9 shape 5); D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4, 4..6 = 32x4 with the pulled
+// d.tile = shape | mode << 4 | chunk << 8: shape 0 = default (D3Q19 shape 7,
+// D2Q9 shape 5); D3Q19 1 = 32x8, 2 = 64x4, 3 = 32x4, 4..7 = 32x4 with the pulled
 // populations of a thread's node staged in shared memory for the collision
 // (4: the 19 f values; 5: lane-shifted values first, 28 for FP32, 19 with the
-// per-warp prefetch for 16-bit storage; 6: 19 lane-shifted values); D2Q9
+// per-warp prefetch for 16-bit storage; 6: 19 lane-shifted values; 7: as 5 in
+// the order of the paired lane words, the k values first, then the
+// lane-shifted (f, g) pairs, so that the collision reloads whole words); D2Q9
 // shape 0 = 5: 128-node rows with all 27 values staged, 1 = 128, 2 = 256, 3 =
 // 64, 4 = 128 with the 18 lane-shifted values staged.  mode (shapes 1..3) bit 0: interleaved border
 // loads; bit 1: early phase-C loads; bit 2: per-warp L2 prefetch three planes
@@ -1013,7 +1023,7 @@ inline FusedCfg<Q> fused_cfg(const tlbm_host::DevState& d) {
         c.TX = 16;  // double storage: a smaller tile keeps the static shared ring small
         c.TY = 8;
     } else if (Q == 19) {
-        const int v = variant == 0 ? 5 : variant;  // 32x4 with staging measured fastest on 256^3
+        const int v = variant == 0 ? 7 : variant;  // 32x4 with pair-aware staging measured fastest on 256^3
         c.TX = v == 2 ? 64 : 32;
         c.TY = v == 1 ? 8 : 4;
         c.shape = v;
@@ -1127,7 +1137,7 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
                 else k_fused_solid<Q, S, 128, 1, true><<<(int)nb, 128, 0, st>>>(g, src, dst, d.nbm, P, d.partials);
             } else {
                 if constexpr (Q == 19) {
-                    const cudaError_t e = launch_staged(k_fused_x<Q, S, 32, 4, 28, 0, 4, false, false, 1, true>, 28, nb,
+                    const cudaError_t e = launch_staged(k_fused_x<Q, S, 32, 4, 28, 2, 4, false, false, 1, true>, 28, nb,
                                                         st, g, src, dst, P, d.partials);
                     if (e != cudaSuccess) return e;
                 } else {
@@ -1164,21 +1174,24 @@ inline cudaError_t fused_step(tlbm_host::DevState& d, const Phys<typename Store<
         if constexpr (sizeof(S) <= 4) {
             if (c.shape >= 4) {
                 // 32x4 kernels with shared-memory staging of the pulled populations:
-                // 4 the 19 f values; 5 (default) the lane-shifted values first, 28
-                // of them for FP32, 19 with the per-warp L2 prefetch for the 16-bit
-                // formats; 6 19 lane-shifted values (no prefetch)
+                // 4 the 19 f values; 5 the lane-shifted values first, 28 of them for
+                // FP32, 19 with the per-warp L2 prefetch for the 16-bit formats; 6
+                // 19 lane-shifted values (no prefetch); 7 (default) as 5 in the
+                // paired-word order (k values, then lane-shifted (f, g) pairs)
                 cudaError_t e;
                 if constexpr (sizeof(S) == 2) {
                     switch (c.shape) {
                         case 4: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 1, 4, false, true, 1>, 19, nb, st, g, src, dst, P, d.partials); break;
                         case 6: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 0, 4, false, false, 1>, 19, nb, st, g, src, dst, P, d.partials); break;
-                        default: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 0, 4, false, true, 1>, 19, nb, st, g, src, dst, P, d.partials);
+                        case 5: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 0, 4, false, true, 1>, 19, nb, st, g, src, dst, P, d.partials); break;
+                        default: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 2, 4, false, true, 1>, 19, nb, st, g, src, dst, P, d.partials);
                     }
                 } else {
                     switch (c.shape) {
                         case 4: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 1, 4, false, false, 1>, 19, nb, st, g, src, dst, P, d.partials); break;
                         case 6: e = launch_staged(k_fused_x<Q, S, 32, 4, 19, 0, 4, false, false, 1>, 19, nb, st, g, src, dst, P, d.partials); break;
-                        default: e = launch_staged(k_fused_x<Q, S, 32, 4, 28, 0, 4, false, false, 1>, 28, nb, st, g, src, dst, P, d.partials);
+                        case 5: e = launch_staged(k_fused_x<Q, S, 32, 4, 28, 0, 4, false, false, 1>, 28, nb, st, g, src, dst, P, d.partials); break;
+                        default: e = launch_staged(k_fused_x<Q, S, 32, 4, 28, 2, 4, false, false, 1>, 28, nb, st, g, src, dst, P, d.partials);
                     }
                 }
                 return e != cudaSuccess ? e : cudaGetLastError();

@@ -178,28 +178,36 @@ __device__ __forceinline__ void guo_collide_node(unsigned char* cb, const typena
     const T src_c = T(1) - T(0.5) * P.omega[0];
     T sf = T(0), sg = T(0), sk = T(0);  // sums of the moving equilibria (deviations)
     T qf = T(0), qg = T(0), qk = T(0);  // sums of the moving populations as stored
+    // opposite directions in pairs, so that the paired lane words are stored whole
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        T e = T(0), eF = T(0);
-        if (Lat<Q>::cx(i)) { e += T(Lat<Q>::cx(i)) * u[0]; eF += T(Lat<Q>::cx(i)) * F[0]; }
-        if (Lat<Q>::cy(i)) { e += T(Lat<Q>::cy(i)) * u[1]; eF += T(Lat<Q>::cy(i)) * F[1]; }
-        if (Lat<Q>::cz(i)) { e += T(Lat<Q>::cz(i)) * u[2]; eF += T(Lat<Q>::cz(i)) * F[2]; }
-        const T w = T(Lat<Q>::w(i));
-        T fe, ge, ke;
-        E.eq(w, e, fe, ge, ke);
-        sf += fe; sg += ge; sk += ke;
-        const T Si = src_c * w * (T(3) * (eF - uF) + T(9) * e * eF);
-        const T vf = f[i] + P.omega[0] * (fe - f[i]) + Si;
-        const T vg = gg[i] + P.omega[1] * (ge - gg[i]);
-        const T vk = k[i] + P.omega[2] * (ke - k[i]);
-        Fmt<Q, S>::st_delta(cb, 0, i, vf);
-        Fmt<Q, S>::st_delta(cb, 1, i, vg);
-        Fmt<Q, S>::st_delta(cb, 2, i, vk);
-        if (OF) {
-            qf += Fmt<Q, S>::qdelta_d(i, vf);
-            qg += Fmt<Q, S>::qdelta_d(i, vg);
-            qk += Fmt<Q, S>::qdelta_d(i, vk);
+        const int o = opp<Q>(i);
+        if (o < i) continue;
+        T vf[2], vg[2], vk[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int d = h ? o : i;
+            T e = T(0), eF = T(0);
+            if (Lat<Q>::cx(d)) { e += T(Lat<Q>::cx(d)) * u[0]; eF += T(Lat<Q>::cx(d)) * F[0]; }
+            if (Lat<Q>::cy(d)) { e += T(Lat<Q>::cy(d)) * u[1]; eF += T(Lat<Q>::cy(d)) * F[1]; }
+            if (Lat<Q>::cz(d)) { e += T(Lat<Q>::cz(d)) * u[2]; eF += T(Lat<Q>::cz(d)) * F[2]; }
+            const T w = T(Lat<Q>::w(d));
+            T fe, ge, ke;
+            E.eq(w, e, fe, ge, ke);
+            sf += fe; sg += ge; sk += ke;
+            const T Si = src_c * w * (T(3) * (eF - uF) + T(9) * e * eF);
+            vf[h] = f[d] + P.omega[0] * (fe - f[d]) + Si;
+            vg[h] = gg[d] + P.omega[1] * (ge - gg[d]);
+            vk[h] = k[d] + P.omega[2] * (ke - k[d]);
+            if (OF) {
+                qf += Fmt<Q, S>::qdelta_d(d, vf[h]);
+                qg += Fmt<Q, S>::qdelta_d(d, vg[h]);
+                qk += Fmt<Q, S>::qdelta_d(d, vk[h]);
+            }
         }
+        Fmt<Q, S>::template st_fg<false>(cb, i, vf[0], vg[0]);
+        Fmt<Q, S>::template st_fg<false>(cb, o, vf[1], vg[1]);
+        Fmt<Q, S>::template st_kk<false>(cb, i, vk[0], vk[1]);
     }
     if (OF) {
         // the source sums to zero over i: the rest population is what keeps
@@ -393,12 +401,14 @@ __device__ __forceinline__ void guo_body(const MGeom& g, const S* __restrict__ s
             for (int i = 0; i < Q; ++i) {
                 const unsigned char* p =
                     srcb + ((long long)zr[1 - A::cm(i)] * g.NB + yb[k][1 - A::cb(i)]) * g.rowstride + xc[k][1 - A::ca(i)];
-                const T f = Fmt<Q, S>::ld_delta(p, 0, i);
+                T f, gp;
+                if (Fmt<Q, S>::PAIRED && i > 0) Fmt<Q, S>::ld_fg(p, i, f, gp);  // one lane word
+                else f = Fmt<Q, S>::ld_delta(p, 0, i), gp = Fmt<Q, S>::ld_delta(p, 1, i);
                 rd += f;
                 if (A::ca(i)) ja += T(A::ca(i)) * f;
                 if (A::cb(i)) jb += T(A::cb(i)) * f;
                 if (A::cm(i)) jm += T(A::cm(i)) * f;
-                phi += Fmt<Q, S>::ld_delta(p, 1, i);
+                phi += gp;
                 psi += Fmt<Q, S>::ld_delta(p, 2, i);
             }
             sm[slot][0][h] = Fmt<Q, S>::OFFSET ? T(1) + rd : rd;
@@ -533,8 +543,12 @@ __device__ __forceinline__ void guo_body(const MGeom& g, const S* __restrict__ s
         for (int i = 0; i < Q; ++i) {
             const unsigned char* p =
                 srcb + ((long long)zr[1 - A::cm(i)] * g.NB + yo[1 - A::cb(i)]) * g.rowstride + xo[1 - A::ca(i)];
-            fv[i] = Fmt<Q, S>::ld_delta(p, 0, i);
-            gv[i] = Fmt<Q, S>::ld_delta(p, 1, i);
+            if (Fmt<Q, S>::PAIRED && i > 0) {
+                Fmt<Q, S>::ld_fg(p, i, fv[i], gv[i]);
+            } else {
+                fv[i] = Fmt<Q, S>::ld_delta(p, 0, i);
+                gv[i] = Fmt<Q, S>::ld_delta(p, 1, i);
+            }
             kv[i] = Fmt<Q, S>::ld_delta(p, 2, i);
         }
         unsigned char* out =

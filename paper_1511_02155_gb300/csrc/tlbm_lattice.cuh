@@ -170,10 +170,13 @@ struct Store<__nv_bfloat16> {
 // Inside a chunk, each run holds one lane word per node, Fmt::ESZ bytes apart,
 // so a node is one byte offset, chunk + lane * ESZ, and every population of it
 // is that offset plus a constant.
-//   FP64 / FP32: 3Q runs of S, run s*Q + i for set s, direction i.  FP32 keeps
-//     f as its deviation f_i - w_i from the rest state at rho = 1 (g and k as
-//     they are): deviations are small, so FP32 rounding of the stored values,
-//     and with it the drift of the total momentum, is ~100x smaller.
+//   FP64, and FP32 on D2Q9: 3Q runs of S, run s*Q + i for set s, direction i.
+//   FP32 on D3Q19: 64-bit lane words of two values, paired as in the 16-bit
+//     formats below ((f_i, g_i), (k_i, k_opp(i))), and the rest populations as
+//     (f_0, g_0) and (k_0, unused).  FP32 keeps f as its deviation f_i - w_i
+//     from the rest state at rho = 1 (g and k as they are): deviations are
+//     small, so FP32 rounding of the stored values, and with it the drift of
+//     the total momentum, is ~100x smaller.
 //   16-bit formats (packed): f is kept as its deviation f_i - w_i from the
 //     rest state at rho = 1, g and k as they are.  Every lane word is 32 bits:
 //     for each moving direction i one run of (f_i, g_i) pairs (the two share a
@@ -205,9 +208,18 @@ struct Fmt {
     // f kept as its deviation f_i - w_i from the rest state at rho = 1 (FP32 and
     // the 16-bit formats; FP64 stores f as it is)
     static constexpr bool OFFSET = sizeof(S) <= 4;
-    static constexpr int ESZ = PACKED ? 4 : (int)sizeof(S);  // bytes between lanes of a run
-    static constexpr int NKP = (Q - 1) / 2;                  // runs of k pairs (packed)
-    static constexpr long long CHUNK = PACKED ? ((Q - 1) + NKP + 3) * 128LL : 3LL * Q * 32 * ESZ;
+    // lane words of two values: the 16-bit formats, and FP32 on D3Q19 (measured:
+    // 0.5 % faster there; on D2Q9, whose kernels run near the HBM limit, the
+    // unused fourth word of the FP32 rest populations costs 5 %); FP64 one value
+    static constexpr bool PAIRED = sizeof(S) == 2 || (sizeof(S) == 4 && Q == 19);
+    static constexpr int VSZ = (int)sizeof(S);              // bytes of one value
+    static constexpr int ESZ = PAIRED ? 2 * VSZ : VSZ;       // bytes between lanes of a run
+    static constexpr int RUN = 32 * ESZ;                     // bytes of a run
+    static constexpr int NKP = (Q - 1) / 2;                  // runs of k pairs
+    // runs of the rest populations: 16-bit formats one FP32 word each; FP32 the
+    // words (f_0, g_0) and (k_0, unused)
+    static constexpr int NREST = PACKED ? 3 : 2;
+    static constexpr long long CHUNK = PAIRED ? (long long)((Q - 1) + NKP + NREST) * RUN : 3LL * Q * 32 * ESZ;
     // packed: run of the k pair of direction i (the pairs of opposite directions
     // numbered by their lower direction), and the half of its lane word (0: i is
     // the lower direction of its pair).  Tables, so that they fold to immediates.
@@ -229,10 +241,13 @@ struct Fmt {
     }
     // byte offset of (s, i) in the lane word of lane 0
     __host__ __device__ static constexpr int off(int s, int i) {
-        if (!PACKED) return (s * Q + i) * 32 * ESZ;
-        if (i == 0) return ((Q - 1) + NKP + s) * 128;
-        if (s < 2) return (i - 1) * 128 + 2 * s;
-        return ((Q - 1) + kpair(i)) * 128 + 2 * khalf(i);
+        if (!PAIRED) return (s * Q + i) * 32 * ESZ;
+        if (i == 0) {
+            if (PACKED) return ((Q - 1) + NKP + s) * RUN;
+            return ((Q - 1) + NKP + (s == 2 ? 1 : 0)) * RUN + (s == 1 ? 4 : 0);
+        }
+        if (s < 2) return (i - 1) * RUN + s * VSZ;
+        return ((Q - 1) + kpair(i)) * RUN + khalf(i) * VSZ;
     }
     // rest-state value subtracted before storage (set f, offset formats)
     __host__ __device__ static constexpr double bias(int s, int i) {
@@ -283,6 +298,11 @@ struct Fmt {
         if constexpr (PACKED) {
             const unsigned* p = reinterpret_cast<const unsigned*>(n + off(0, i));
             Store<S>::get2(LAST ? __ldcs(p) : *p, f, g);
+        } else if constexpr (PAIRED) {
+            const float2* p = reinterpret_cast<const float2*>(n + off(0, i));
+            const float2 v = LAST ? __ldcs(p) : *p;
+            f = v.x;
+            g = v.y;
         } else {
             f = LAST ? ld_last_delta(n, 0, i) : ld_delta(n, 0, i);
             g = LAST ? ld_last_delta(n, 1, i) : ld_delta(n, 1, i);
@@ -331,6 +351,11 @@ struct Fmt {
             const unsigned w = Store<S>::put2(df, dg);
             if (STREAM) __stcs(p, w);
             else *p = w;
+        } else if constexpr (PAIRED) {
+            float2* p = reinterpret_cast<float2*>(n + off(0, i));
+            const float2 w = make_float2(df, dg);
+            if (STREAM) __stcs(p, w);
+            else *p = w;
         } else if (STREAM) {
             st_stream_delta(n, 0, i, df);
             st_stream_delta(n, 1, i, dg);
@@ -345,6 +370,12 @@ struct Fmt {
             const bool lo = khalf(i) == 0;  // the lower direction sits in the low half
             unsigned* p = reinterpret_cast<unsigned*>(n + off(2, lo ? i : opp<Q>(i)));
             const unsigned w = lo ? Store<S>::put2(dki, dko) : Store<S>::put2(dko, dki);
+            if (STREAM) __stcs(p, w);
+            else *p = w;
+        } else if constexpr (PAIRED) {
+            const bool lo = khalf(i) == 0;
+            float2* p = reinterpret_cast<float2*>(n + off(2, lo ? i : opp<Q>(i)));
+            const float2 w = lo ? make_float2(dki, dko) : make_float2(dko, dki);
             if (STREAM) __stcs(p, w);
             else *p = w;
         } else if (STREAM) {
