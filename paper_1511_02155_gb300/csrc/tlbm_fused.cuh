@@ -747,6 +747,7 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
     };
 
     constexpr bool PAIR = Fmt<Q, S>::OFFSET && !(Q == 19 && sizeof(S) == 4);
+    constexpr bool HL = sizeof(S) == 4;  // evict-first hints in the collision
     MassSum<T, PAIR> msum;
 
     moments_plane(M0 - 2);
@@ -824,16 +825,18 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
             const bool bb = i > 0 && ((mk >> i) & 1u);
             const unsigned char* pfg = bb ? own + (Fmt<Q, S>::off(0, opp<Q>(i)) - Fmt<Q, S>::off(0, i)) : p;
             const unsigned char* pk = bb ? own + (Fmt<Q, S>::off(2, opp<Q>(i)) - Fmt<Q, S>::off(2, i)) : p;
+            // the collision is the last reader of these lines: evict-first loads
+            // (FP32 storage; measured slower for the 16-bit formats)
             if (i > 0) {
                 T df, dg;
-                Fmt<Q, S>::ld_fg(pfg, i, df, dg);
+                Fmt<Q, S>::template ld_fg<HL>(pfg, i, df, dg);
                 fv[i] = Fmt<Q, S>::unbias(0, i, df);
                 gv[i] = dg;
             } else {
-                fv[i] = Fmt<Q, S>::ld(p, 0, 0);
-                gv[i] = Fmt<Q, S>::ld(p, 1, 0);
+                fv[i] = HL ? Fmt<Q, S>::ld_last(p, 0, 0) : Fmt<Q, S>::ld(p, 0, 0);
+                gv[i] = HL ? Fmt<Q, S>::ld_last(p, 1, 0) : Fmt<Q, S>::ld(p, 1, 0);
             }
-            kv[i] = Fmt<Q, S>::ld(pk, 2, i);
+            kv[i] = HL ? Fmt<Q, S>::ld_last(pk, 2, i) : Fmt<Q, S>::ld(pk, 2, i);
         }
 
         // ---- collide + store (same arithmetic as k_fused)
@@ -863,23 +866,28 @@ __device__ __forceinline__ void solid_body(const MGeom& g, const S* __restrict__
             const T v[6] = {cf * fv[i] + (evf + odf), cf * fv[o] + (evf - odf),
                             cg * gv[i] + (evg + odg), cg * gv[o] + (evg - odg),
                             ck * kv[i] + (evk + odk), ck * kv[o] + (evk - odk)};
-            Fmt<Q, S>::template st_fg<false>(out, i, Fmt<Q, S>::dev(0, i, v[0]), v[2]);
-            Fmt<Q, S>::template st_fg<false>(out, o, Fmt<Q, S>::dev(0, o, v[1]), v[3]);
-            Fmt<Q, S>::template st_kk<false>(out, i, v[4], v[5]);
+            // streamed out (evict-first, FP32): read only by the next step
+            Fmt<Q, S>::template st_fg<HL>(out, i, Fmt<Q, S>::dev(0, i, v[0]), v[2]);
+            Fmt<Q, S>::template st_fg<HL>(out, o, Fmt<Q, S>::dev(0, o, v[1]), v[3]);
+            Fmt<Q, S>::template st_kk<HL>(out, i, v[4], v[5]);
             if (Fmt<Q, S>::OFFSET) {
                 qf += Fmt<Q, S>::qdelta(0, i, v[0]) + Fmt<Q, S>::qdelta(0, o, v[1]);
                 qg += Fmt<Q, S>::qdelta(1, i, v[2]) + Fmt<Q, S>::qdelta(1, o, v[3]);
                 qk += Fmt<Q, S>::qdelta(2, i, v[4]) + Fmt<Q, S>::qdelta(2, o, v[5]);
             }
         }
+        auto st_rest = [&](int s_, T d) {
+            if (HL) Fmt<Q, S>::st_stream_delta(out, s_, 0, d);
+            else Fmt<Q, S>::st_delta(out, s_, 0, d);
+        };
         if (Fmt<Q, S>::OFFSET) {
-            Fmt<Q, S>::st_delta(out, 0, 0, rdc - qf);
-            Fmt<Q, S>::st_delta(out, 1, 0, E.phi - qg);
-            Fmt<Q, S>::st_delta(out, 2, 0, E.psi - qk);
+            st_rest(0, rdc - qf);
+            st_rest(1, E.phi - qg);
+            st_rest(2, E.psi - qk);
         } else {
-            Fmt<Q, S>::st(out, 0, 0, cf * fv[0] + (P.omega[0] * E.rho - sf));
-            Fmt<Q, S>::st(out, 1, 0, cg * gv[0] + (P.omega[1] * E.phi - sg));
-            Fmt<Q, S>::st(out, 2, 0, ck * kv[0] + (P.omega[2] * E.psi - sk2));
+            st_rest(0, Fmt<Q, S>::dev(0, 0, cf * fv[0] + (P.omega[0] * E.rho - sf)));
+            st_rest(1, cg * gv[0] + (P.omega[1] * E.phi - sg));
+            st_rest(2, ck * kv[0] + (P.omega[2] * E.psi - sk2));
         }
     }
 
