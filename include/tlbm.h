@@ -206,7 +206,10 @@ tlbm_status tlbm_set_populations(tlbm *t, const double *host);
 size_t tlbm_state_bytes(const tlbm *t);
 
 /* Copy the raw device state to / from host memory of tlbm_state_bytes bytes.
- * A state saved by tlbm_get_state resumes bitwise identically.  Synchronises. */
+ * A state saved by tlbm_get_state resumes bitwise identically.  The bytes are
+ * the device layout of this library build (chunked lane words per storage
+ * format and lattice), not an interchange format: use tlbm_get_populations /
+ * tlbm_set_populations to move a state between builds.  Synchronises. */
 tlbm_status tlbm_get_state(tlbm *t, void *host, size_t bytes);
 tlbm_status tlbm_set_state(tlbm *t, const void *host, size_t bytes);
 
