@@ -491,10 +491,14 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
                 const T v[6] = {cf * fv[i] + (evf + odf), cf * fv[o] + (evf - odf),
                                 cg * gv[i] + (evg + odg), cg * gv[o] + (evg - odg),
                                 ck * kv[i] + (evk + odk), ck * kv[o] + (evk - odk)};
-                if constexpr (Fmt<Q, S>::PAIRED) {  // three lane words
-                    Fmt<Q, S>::template st_fg<(HINT >= 1)>(out, i, v[0], v[2]);
-                    Fmt<Q, S>::template st_fg<(HINT >= 1)>(out, o, v[1], v[3]);
-                    Fmt<Q, S>::template st_kk<(HINT >= 1)>(out, i, v[4], v[5]);
+                if constexpr (Fmt<Q, S>::PAIRED) {  // three lane words (all offset formats)
+                    T q[6];  // the deviations as stored
+                    Fmt<Q, S>::template st_fg_q<(HINT >= 1)>(out, i, v[0], v[2], q[0], q[2]);
+                    Fmt<Q, S>::template st_fg_q<(HINT >= 1)>(out, o, v[1], v[3], q[1], q[3]);
+                    Fmt<Q, S>::template st_kk_q<(HINT >= 1)>(out, i, v[4], v[5], q[4], q[5]);
+                    qf += q[0] + q[1];
+                    qg += q[2] + q[3];
+                    qk += q[4] + q[5];
                 } else {
                     st_(out, 0, i, v[0]);
                     st_(out, 0, o, v[1]);
@@ -502,11 +506,11 @@ __device__ __forceinline__ void fused_body(const MGeom& g, const S* __restrict__
                     st_(out, 1, o, v[3]);
                     st_(out, 2, i, v[4]);
                     st_(out, 2, o, v[5]);
-                }
-                if (OF) {
-                    qf += Fmt<Q, S>::qdelta_d(i, v[0]) + Fmt<Q, S>::qdelta_d(o, v[1]);
-                    qg += Fmt<Q, S>::qdelta_d(i, v[2]) + Fmt<Q, S>::qdelta_d(o, v[3]);
-                    qk += Fmt<Q, S>::qdelta_d(i, v[4]) + Fmt<Q, S>::qdelta_d(o, v[5]);
+                    if (OF) {
+                        qf += Fmt<Q, S>::qdelta_d(i, v[0]) + Fmt<Q, S>::qdelta_d(o, v[1]);
+                        qg += Fmt<Q, S>::qdelta_d(i, v[2]) + Fmt<Q, S>::qdelta_d(o, v[3]);
+                        qk += Fmt<Q, S>::qdelta_d(i, v[4]) + Fmt<Q, S>::qdelta_d(o, v[5]);
+                    }
                 }
             }
             if (OF) {

@@ -386,6 +386,38 @@ struct Fmt {
             st_delta(n, 2, opp<Q>(i), dko);
         }
     }
+    // st_fg / st_kk that also return the deviations as stored (read back from
+    // the lane word itself: no second conversion of each value)
+    template <bool STREAM>
+    static __device__ __forceinline__ void st_fg_q(unsigned char* n, int i, T df, T dg, T& qf, T& qg) {
+        if constexpr (PACKED) {
+            unsigned* p = reinterpret_cast<unsigned*>(n + off(0, i));
+            const unsigned w = Store<S>::put2(df, dg);
+            if (STREAM) __stcs(p, w);
+            else *p = w;
+            Store<S>::get2(w, qf, qg);
+        } else {
+            st_fg<STREAM>(n, i, df, dg);
+            qf = df;
+            qg = dg;
+        }
+    }
+    template <bool STREAM>
+    static __device__ __forceinline__ void st_kk_q(unsigned char* n, int i, T dki, T dko, T& qi, T& qo) {
+        if constexpr (PACKED) {
+            const bool lo = khalf(i) == 0;
+            unsigned* p = reinterpret_cast<unsigned*>(n + off(2, lo ? i : opp<Q>(i)));
+            const unsigned w = lo ? Store<S>::put2(dki, dko) : Store<S>::put2(dko, dki);
+            if (STREAM) __stcs(p, w);
+            else *p = w;
+            if (lo) Store<S>::get2(w, qi, qo);
+            else Store<S>::get2(w, qo, qi);
+        } else {
+            st_kk<STREAM>(n, i, dki, dko);
+            qi = dki;
+            qo = dko;
+        }
+    }
     // the deviation a store of population value v leaves in memory, as read back
     static __device__ __forceinline__ T qdelta(int s, int i, T v) {
         const double b = bias(s, i);
